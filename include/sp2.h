@@ -1,0 +1,179 @@
+/*
+ * sp2.h -- C ABI of a GB300 (sm_103a) library that computes the zero-temperature
+ * density matrix D of a symmetric block-sparse Fock/Kohn-Sham matrix F with the
+ * SP2ACC recursive expansion and error-controlled truncation.
+ *
+ * Paper: A. Kruchinina, E. Rudberg, E. H. Rubensson, "Efficient computation of the
+ * density matrix with error control on distributed computer systems",
+ * arXiv:1909.12533.  Section 1 defines D (Eq. (3): projector onto the nocc lowest
+ * eigenvectors of F); Section 4 gives the method: Step 1 (schedule, Gershgorin
+ * bounds, Algorithm 1), Step 2 (Algorithm 2: X_i = ((1-a)I + a X~)^2 or
+ * 2aX~ - (aX~)^2, truncation X~_i = X_i + E_i, e_i = ||X~_i - X~_i^2||_F,
+ * t_i = trace(X~_i - X~_i^2), parameterless stop with C = 6.8872), Step 3
+ * (homo/lumo estimates from e_i and t_i).  Section 2 gives the truncation error
+ * control (Eqs. (6)-(8)), Section 3 the Frob-Inf norm (Eq. (13)).
+ *
+ * Conventions (all entry points):
+ *  - Every function returns SP2_OK (0) or a negative SP2_ERR_* code; no C++
+ *    exception crosses this boundary.  sp2_strerror() names a code.
+ *  - Matrices are exchanged as sp2_bsr: tiles of b x b with b = 32, only tiles
+ *    with block row <= block column stored, sorted by (row, col), values
+ *    row-major inside each tile, diagonal tiles stored in full (both triangles),
+ *    every diagonal tile present.  When N is not a multiple of 32 the last tile
+ *    row/column is zero padding and stays zero.
+ *  - All GPU work is issued on the caller's CUDA stream (cudaStream_t passed as
+ *    void*; NULL = legacy default stream).  Calls synchronise that stream only
+ *    where they need a scalar on the host (counts, e_i / t_i for the stop test).
+ *  - The context owns all device memory it allocates.  Inputs are copied;
+ *    the caller keeps ownership of its buffers.
+ *  - Not thread-safe per context; different contexts are independent.
+ */
+#ifndef SP2_H
+#define SP2_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---------------------------------------------------------------- status codes */
+#define SP2_OK                 0
+#define SP2_ERR_INVALID_ARG   -1  /* NULL pointer, bad size, b != 32, bad enum     */
+#define SP2_ERR_BOUNDS        -2  /* homo_ub >= lumo_lb, or bounds outside [lmin, lmax] */
+#define SP2_ERR_PATTERN       -3  /* tiles unsorted, lower-triangle, out of range, missing diagonal tile */
+#define SP2_ERR_NONFINITE     -4  /* NaN or Inf in F (or W)                        */
+#define SP2_ERR_OOM           -5  /* device allocation failed                      */
+#define SP2_ERR_CUDA          -6  /* a CUDA runtime call failed                    */
+#define SP2_ERR_NOT_CONVERGED -7  /* n_max reached without the stop test firing; D is still readable */
+#define SP2_ERR_TIMEOUT       -8  /* a bounded device wait gave up                 */
+#define SP2_ERR_STATE         -9  /* call out of order (e.g. get_D before run)     */
+#define SP2_ERR_CAPACITY     -10  /* caller buffer too small (size returned)       */
+
+#define SP2_TILE 32
+#define SP2_MAX_ITER 128
+
+/* ---------------------------------------------------------------- enums */
+enum sp2_mode      { SP2_MODE_SP2 = 0, SP2_MODE_SP2ACC = 1 };
+/* Stop tests: Algorithm 2's parameterless criterion, or e_j < idem_tol. */
+enum sp2_stop      { SP2_STOP_PARAMETERLESS = 0, SP2_STOP_IDEMPOTENCY = 1 };
+/* Truncation norm: Frobenius (Section 2) or Frob-Inf (Section 3, Eq. (13)). */
+enum sp2_trunc     { SP2_TRUNC_FROBENIUS = 0, SP2_TRUNC_FROBINF = 1 };
+/* Arithmetic of the tile products X~ X~:
+ *   FP64   : FP64 fused multiply-adds on the CUDA cores.
+ *   SPLIT16: tcgen05 tensor-core MMAs on FP16 slices of X~ on fixed absolute
+ *            grids (slice s on the grid 2^-(11 s - 1)); products of slice pairs
+ *            (s, t) with s + t <= slices + 1 accumulate exactly-grouped in FP32
+ *            tensor memory and are combined in FP64.  slices = 2 is the
+ *            hi+lo three-product form.
+ * Everything else (traces, norms, polynomial choice, stop test, truncation)
+ * is FP64 in every precision. */
+enum sp2_precision { SP2_PREC_FP64 = 0, SP2_PREC_SPLIT16 = 1 };
+
+typedef struct {
+  int64_t n;              /* matrix dimension N                                  */
+  int32_t b;              /* tile size; must be 32                               */
+  int64_t nnzb;           /* number of stored tiles                              */
+  const int32_t* brow;    /* [nnzb] tile row I                                   */
+  const int32_t* bcol;    /* [nnzb] tile column J >= I                           */
+  const double* val;      /* [nnzb * b * b] tile values, row-major per tile      */
+  int32_t on_device;      /* 1: the three pointers are device pointers; 0: host  */
+} sp2_bsr;
+
+/* Optional device allocator.  alloc returns NULL on failure (-> SP2_ERR_OOM).
+ * NULL allocator = cudaMallocAsync / cudaFreeAsync on the context's stream. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} sp2_allocator;
+
+typedef struct {
+  int32_t mode;            /* sp2_mode, default SP2ACC                                  */
+  int32_t stop;            /* sp2_stop, default PARAMETERLESS                           */
+  double idem_tol;         /* threshold of the idempotency stop, default 1e-12          */
+  int32_t trunc;           /* sp2_trunc, default FROBENIUS                              */
+  int64_t frobinf_part;    /* Frob-Inf partition size in rows, multiple of 32; default 4096 (Section 6) */
+  double gamma;            /* > 0: tau_i from Eq. (7) with this gamma; tau argument ignored */
+  double delta_acc;        /* acceleration switches off once max distance <= delta_acc; default 0.1 */
+  int32_t n_max_cap;       /* cap on n_max, <= SP2_MAX_ITER - 2; default 100             */
+  int32_t precision;       /* sp2_precision, default FP64                               */
+  int32_t slices;          /* SPLIT16 slices, 2..4, default 4                            */
+  int32_t mixed_from;      /* first iteration i whose square uses `precision` (earlier ones FP64); default 1 */
+  int32_t mixed_until;     /* last iteration using `precision` (later ones FP64); 0 = no limit */
+  int32_t ckpt_every;      /* adjoint checkpoint interval k (X~_i kept for i % k == 0); default 8 */
+  int32_t record_masks;    /* 1: keep per-iteration tile masks (needed by sp2_backward); default 1 */
+} sp2_params;
+
+typedef struct {
+  int32_t status;          /* return code of the last sp2_run                          */
+  int32_t converged;       /* 1 when the stop test fired                               */
+  int32_t n;               /* index n of the returned iterate X~_n                     */
+  int32_t n_min, n_max;    /* schedule (Section 4, Step 1)                             */
+  int32_t squares;         /* matrix squares computed (n + 1)                          */
+  double lmin, lmax;       /* Gershgorin bounds (Algorithm 1)                          */
+  double homo_est, lumo_est; /* Step 3 estimates (NaN when unavailable)                 */
+  int32_t have_estimates;  /* bit 0: homo_est valid, bit 1: lumo_est valid */
+  int64_t nnzb_final;      /* stored tiles of D                                        */
+  int64_t tile_triplets;   /* sum over squares of (I <= J, K) tile triplets             */
+  double alg_flops;        /* 2 * 32^3 * tile_triplets                                 */
+  double run_ms;           /* device time of sp2_run (cudaEvents)                      */
+  double square_ms;        /* device time spent in the tile-product kernels            */
+  int32_t p[SP2_MAX_ITER];        /* p_i, i = 1..n_max (p[0] unused = -1)              */
+  double alpha[SP2_MAX_ITER];     /* alpha_i                                           */
+  double tau[SP2_MAX_ITER];       /* tau_i, i = 0..n_max                               */
+  double e[SP2_MAX_ITER];         /* e_j, j = 0..n                                     */
+  double t[SP2_MAX_ITER];         /* t_j                                               */
+  int64_t nnzb_hist[SP2_MAX_ITER]; /* stored tiles of X~_j                             */
+  int32_t prec_hist[SP2_MAX_ITER]; /* precision of the square that produced e_j         */
+} sp2_stats;
+
+typedef struct sp2_ctx sp2_ctx;
+
+/* Fill *p with the defaults listed above. */
+int sp2_default_params(sp2_params* p);
+
+/* Step 1 of Section 4 (and Algorithm 1): copy F to the device, compute the
+ * Gershgorin bounds lmin <= lambda_1, lmax >= lambda_N, build the schedule
+ * (p_i, alpha_i, n_min, n_max, tau_i) from homo_ub >= lambda_homo and
+ * lumo_lb <= lambda_lumo, form X_0 = (lmax I - F)/(lmax - lmin) and its
+ * truncation X~_0.  tau is the truncation threshold of every iteration
+ * (ignored when params->gamma > 0).  nocc is used for reporting only.
+ * Errors: INVALID_ARG, PATTERN, NONFINITE, BOUNDS, OOM, CUDA.  On error *out is NULL. */
+int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, double tau,
+               const sp2_params* params, const sp2_allocator* alloc, void* cuda_stream,
+               sp2_ctx** out);
+
+/* Step 2 of Section 4 (Algorithm 2) and Step 3: iterate until the stop test
+ * fires, then estimate homo/lumo.  Returns SP2_OK, SP2_ERR_NOT_CONVERGED (D is
+ * the last iterate and readable), or an error.  stats may be NULL. */
+int sp2_run(sp2_ctx* ctx, sp2_stats* stats);
+
+/* Borrowed device view of D (tile arrays owned by ctx, valid until the next
+ * sp2_run, sp2_backward or sp2_destroy).  view->on_device = 1. */
+int sp2_get_D(sp2_ctx* ctx, sp2_bsr* view);
+
+/* Copy D's tiles to caller buffers (host or device per `on_device`).  If
+ * cap_nnzb is smaller than D's tile count, nothing is copied, *nnzb_out is set
+ * and SP2_ERR_CAPACITY returned. */
+int sp2_copy_D(sp2_ctx* ctx, int32_t* brow, int32_t* bcol, double* val, int64_t cap_nnzb,
+               int32_t on_device, int64_t* nnzb_out);
+
+/* Reverse-mode derivative of L = trace(D W) (not in the paper): W symmetric,
+ * given on any tile pattern (only tiles of D's pattern matter).  Writes
+ * dF = dL/dF on F's tile pattern (F's brow/bcol order; entries F_ij and F_ji
+ * treated as independent, so a symmetric perturbation of an off-diagonal pair
+ * changes L by 2 h dF_ij) into a borrowed device view (same lifetime rules as
+ * sp2_get_D).  The iterates are recomputed from checkpoints every ckpt_every
+ * steps with the recorded truncation masks.  Requires record_masks = 1. */
+int sp2_backward(sp2_ctx* ctx, const sp2_bsr* W, sp2_bsr* dF_view);
+
+int sp2_get_stats(const sp2_ctx* ctx, sp2_stats* stats);
+void sp2_destroy(sp2_ctx* ctx);
+const char* sp2_strerror(int code);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SP2_H */

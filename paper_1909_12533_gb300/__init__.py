@@ -1,0 +1,330 @@
+"""Python binding of the SP2 C ABI (include/sp2.h).
+
+Argument marshalling only: every step of the expansion runs inside
+``libsp2.so`` (CUDA kernels for sm_103a plus the host driver).  The library must
+be built (``python -m paper_1909_12533_gb300.build``); there is no fallback.
+
+Low level: ``sp2_default_params``, ``sp2_create``, ``sp2_run``, ``sp2_get_D``,
+``sp2_copy_D``, ``sp2_backward``, ``sp2_get_stats``, ``sp2_destroy``,
+``sp2_strerror`` mirror the C entry points.  ``SP2`` wraps one context and
+``SP2Function`` is the ``torch.autograd.Function`` (L = trace(D W)).
+"""
+from __future__ import annotations
+
+import ctypes
+from ctypes import POINTER, byref, c_double, c_int32, c_int64, c_size_t, c_void_p
+from pathlib import Path
+
+import numpy as np
+
+TILE = 32
+MAX_ITER = 128
+
+SP2_OK = 0
+ERRORS = {
+    -1: "SP2_ERR_INVALID_ARG", -2: "SP2_ERR_BOUNDS", -3: "SP2_ERR_PATTERN", -4: "SP2_ERR_NONFINITE",
+    -5: "SP2_ERR_OOM", -6: "SP2_ERR_CUDA", -7: "SP2_ERR_NOT_CONVERGED", -8: "SP2_ERR_TIMEOUT",
+    -9: "SP2_ERR_STATE", -10: "SP2_ERR_CAPACITY",
+}
+NOT_CONVERGED = -7
+MODES = {"sp2": 0, "sp2acc": 1}
+STOPS = {"parameterless": 0, "idempotency": 1}
+TRUNCS = {"frobenius": 0, "frobinf": 1}
+PRECISIONS = {"fp64": 0, "split16": 1}
+
+
+class sp2_bsr(ctypes.Structure):
+    _fields_ = [("n", c_int64), ("b", c_int32), ("nnzb", c_int64), ("brow", c_void_p), ("bcol", c_void_p),
+                ("val", c_void_p), ("on_device", c_int32)]
+
+
+class sp2_allocator(ctypes.Structure):
+    _fields_ = [("alloc", c_void_p), ("free", c_void_p), ("user", c_void_p)]
+
+
+class sp2_params(ctypes.Structure):
+    _fields_ = [("mode", c_int32), ("stop", c_int32), ("idem_tol", c_double), ("trunc", c_int32),
+                ("frobinf_part", c_int64), ("gamma", c_double), ("delta_acc", c_double), ("n_max_cap", c_int32),
+                ("precision", c_int32), ("slices", c_int32), ("mixed_from", c_int32), ("mixed_until", c_int32),
+                ("ckpt_every", c_int32), ("record_masks", c_int32)]
+
+
+class sp2_stats(ctypes.Structure):
+    _fields_ = [("status", c_int32), ("converged", c_int32), ("n", c_int32), ("n_min", c_int32), ("n_max", c_int32),
+                ("squares", c_int32), ("lmin", c_double), ("lmax", c_double), ("homo_est", c_double),
+                ("lumo_est", c_double), ("have_estimates", c_int32), ("nnzb_final", c_int64),
+                ("tile_triplets", c_int64), ("alg_flops", c_double), ("run_ms", c_double), ("square_ms", c_double),
+                ("p", c_int32 * MAX_ITER), ("alpha", c_double * MAX_ITER), ("tau", c_double * MAX_ITER),
+                ("e", c_double * MAX_ITER), ("t", c_double * MAX_ITER), ("nnzb_hist", c_int64 * MAX_ITER),
+                ("prec_hist", c_int32 * MAX_ITER)]
+
+
+# Entry points declared in include/sp2.h: (name, restype, argtypes)
+_SIGS = [
+    ("sp2_default_params", c_int32, [POINTER(sp2_params)]),
+    ("sp2_create", c_int32, [POINTER(sp2_bsr), c_int64, c_double, c_double, c_double, POINTER(sp2_params),
+                             POINTER(sp2_allocator), c_void_p, POINTER(c_void_p)]),
+    ("sp2_run", c_int32, [c_void_p, POINTER(sp2_stats)]),
+    ("sp2_get_D", c_int32, [c_void_p, POINTER(sp2_bsr)]),
+    ("sp2_copy_D", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, POINTER(c_int64)]),
+    ("sp2_backward", c_int32, [c_void_p, POINTER(sp2_bsr), POINTER(sp2_bsr)]),
+    ("sp2_get_stats", c_int32, [c_void_p, POINTER(sp2_stats)]),
+    ("sp2_destroy", None, [c_void_p]),
+    ("sp2_strerror", ctypes.c_char_p, [c_int32]),
+]
+
+_LIB = None
+
+
+def lib_path() -> Path:
+    return Path(__file__).with_name("libsp2.so")
+
+
+def load() -> ctypes.CDLL:
+    """Load libsp2.so (raises if it has not been built; there is no fallback)."""
+    global _LIB
+    if _LIB is None:
+        p = lib_path()
+        if not p.exists():
+            raise RuntimeError(f"{p} is missing: build it with `python -m paper_1909_12533_gb300.build`")
+        lib = ctypes.CDLL(str(p))
+        for name, res, args in _SIGS:
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _LIB = lib
+    return _LIB
+
+
+class SP2Error(RuntimeError):
+    def __init__(self, code: int, where: str):
+        self.code = code
+        super().__init__(f"{where}: {ERRORS.get(code, code)} ({sp2_strerror(code)})")
+
+
+def sp2_strerror(code: int) -> str:
+    return load().sp2_strerror(code).decode()
+
+
+def sp2_default_params(**overrides) -> sp2_params:
+    p = sp2_params()
+    rc = load().sp2_default_params(byref(p))
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_default_params")
+    enums = {"mode": MODES, "stop": STOPS, "trunc": TRUNCS, "precision": PRECISIONS}
+    for k, v in overrides.items():
+        if k in enums and isinstance(v, str):
+            v = enums[k][v]
+        setattr(p, k, v)
+    return p
+
+
+# ------------------------------------------------------------------ marshalling
+def _ptr(a):
+    """(pointer, on_device) of a numpy array or torch tensor (kept alive by caller)."""
+    if isinstance(a, np.ndarray):
+        return a.ctypes.data, 0
+    return int(a.data_ptr()), 1 if a.is_cuda else 0
+
+
+def make_bsr(n: int, brow, bcol, val) -> tuple[sp2_bsr, tuple]:
+    """Build an sp2_bsr over numpy arrays or torch tensors (int32, int32, float64,
+    contiguous).  Returns the struct and the objects that must stay alive."""
+    if isinstance(brow, np.ndarray):
+        brow = np.ascontiguousarray(brow, dtype=np.int32)
+        bcol = np.ascontiguousarray(bcol, dtype=np.int32)
+        val = np.ascontiguousarray(val, dtype=np.float64)
+    else:
+        import torch
+        brow = brow.to(torch.int32).contiguous()
+        bcol = bcol.to(torch.int32).contiguous()
+        val = val.to(torch.float64).contiguous()
+    pb, d1 = _ptr(brow)
+    pc, d2 = _ptr(bcol)
+    pv, d3 = _ptr(val)
+    if not (d1 == d2 == d3):
+        raise ValueError("brow, bcol and val must all be host or all be device buffers")
+    s = sp2_bsr(n=int(n), b=TILE, nnzb=int(brow.shape[0]), brow=pb, bcol=pc, val=pv, on_device=d1)
+    return s, (brow, bcol, val)
+
+
+def _stream_handle(stream):
+    if stream is not None:
+        return c_void_p(int(stream))
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return c_void_p(int(torch.cuda.current_stream().cuda_stream))
+    except Exception:  # pragma: no cover - torch missing
+        pass
+    return c_void_p(0)
+
+
+def sp2_create(F, nocc: int, homo_ub: float, lumo_lb: float, tau: float, params: sp2_params | None = None,
+               stream=None) -> c_void_p:
+    """F: object with n, brow, bcol, val (numpy -> host copy, CUDA tensors -> device copy)."""
+    bsr, keep = make_bsr(F.n, F.brow, F.bcol, F.val)
+    ctx = c_void_p()
+    prm = params if params is not None else sp2_default_params()
+    rc = load().sp2_create(byref(bsr), int(nocc), float(homo_ub), float(lumo_lb), float(tau), byref(prm), None,
+                           _stream_handle(stream), byref(ctx))
+    del keep
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_create")
+    return ctx
+
+
+def sp2_run(ctx) -> tuple[int, sp2_stats]:
+    st = sp2_stats()
+    rc = load().sp2_run(ctx, byref(st))
+    if rc not in (SP2_OK, NOT_CONVERGED):
+        raise SP2Error(rc, "sp2_run")
+    return rc, st
+
+
+def sp2_get_D(ctx) -> sp2_bsr:
+    v = sp2_bsr()
+    rc = load().sp2_get_D(ctx, byref(v))
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_get_D")
+    return v
+
+
+def sp2_copy_D(ctx):
+    """Host copy of D: (brow, bcol, val) numpy arrays."""
+    n = c_int64()
+    rc = load().sp2_copy_D(ctx, None, None, None, 0, 0, byref(n))
+    if rc not in (SP2_OK, -10):
+        raise SP2Error(rc, "sp2_copy_D")
+    brow = np.empty(n.value, np.int32)
+    bcol = np.empty(n.value, np.int32)
+    val = np.empty((n.value, TILE, TILE), np.float64)
+    rc = load().sp2_copy_D(ctx, brow.ctypes.data, bcol.ctypes.data, val.ctypes.data, n.value, 0, byref(n))
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_copy_D")
+    return brow, bcol, val
+
+
+def sp2_backward(ctx, W) -> sp2_bsr:
+    bsr, keep = make_bsr(W.n, W.brow, W.bcol, W.val)
+    out = sp2_bsr()
+    rc = load().sp2_backward(ctx, byref(bsr), byref(out))
+    del keep
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_backward")
+    return out
+
+
+def sp2_get_stats(ctx) -> sp2_stats:
+    st = sp2_stats()
+    rc = load().sp2_get_stats(ctx, byref(st))
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_get_stats")
+    return st
+
+
+def sp2_destroy(ctx) -> None:
+    if ctx:
+        load().sp2_destroy(ctx)
+
+
+def stats_dict(st: sp2_stats) -> dict:
+    n = st.n
+    sq = st.squares
+    d = {k: getattr(st, k) for k, *_ in sp2_stats._fields_ if k not in
+         ("p", "alpha", "tau", "e", "t", "nnzb_hist", "prec_hist")}
+    nm = st.n_max
+    d["p"] = [st.p[i] for i in range(nm + 1)]
+    d["alpha"] = [st.alpha[i] for i in range(nm + 1)]
+    d["tau"] = [st.tau[i] for i in range(nm + 1)]
+    d["e"] = [st.e[i] for i in range(sq)]
+    d["t"] = [st.t[i] for i in range(sq)]
+    d["nnzb_hist"] = [st.nnzb_hist[i] for i in range(max(n + 1, 0))]
+    d["prec_hist"] = [st.prec_hist[i] for i in range(sq)]
+    return d
+
+
+def device_view_to_torch(v: sp2_bsr):
+    """Copy a borrowed device view into fresh torch CUDA tensors (brow, bcol, val)."""
+    import torch
+    n = v.nnzb
+    brow = torch.empty(n, dtype=torch.int32, device="cuda")
+    bcol = torch.empty(n, dtype=torch.int32, device="cuda")
+    val = torch.empty((n, TILE, TILE), dtype=torch.float64, device="cuda")
+    cudart = _cudart()
+    for dst, src, nbytes in ((brow, v.brow, n * 4), (bcol, v.bcol, n * 4), (val, v.val, n * TILE * TILE * 8)):
+        if nbytes:
+            rc = cudart.cudaMemcpyAsync(c_void_p(dst.data_ptr()), c_void_p(src), c_size_t(nbytes), 3,
+                                        c_void_p(torch.cuda.current_stream().cuda_stream))
+            if rc != 0:
+                raise RuntimeError(f"cudaMemcpyAsync failed ({rc})")
+    return brow, bcol, val
+
+
+_CUDART = None
+
+
+def _cudart():
+    global _CUDART
+    if _CUDART is None:
+        import glob
+        import torch  # noqa: F401  (loads the runtime torch was built with)
+        cands = ["libcudart.so.13", "libcudart.so.12", "libcudart.so"]
+        for c in cands:
+            try:
+                _CUDART = ctypes.CDLL(c)
+                break
+            except OSError:
+                continue
+        if _CUDART is None:
+            for g in glob.glob("/usr/local/cuda/lib64/libcudart.so*"):
+                _CUDART = ctypes.CDLL(g)
+                break
+        _CUDART.cudaMemcpyAsync.argtypes = [c_void_p, c_void_p, c_size_t, c_int32, c_void_p]
+        _CUDART.cudaMemcpyAsync.restype = c_int32
+    return _CUDART
+
+
+# ------------------------------------------------------------------ convenience
+class SP2:
+    """One SP2 context: create on construction, ``run()``, ``D_host()``,
+    ``D_device()``, ``backward(W)``, ``close()``."""
+
+    def __init__(self, F, nocc, homo_ub, lumo_lb, tau, stream=None, **params):
+        self.prm = sp2_default_params(**params)
+        self.F = F
+        self.ctx = sp2_create(F, nocc, homo_ub, lumo_lb, tau, self.prm, stream)
+        self.code = None
+        self.stats = None
+
+    def run(self) -> dict:
+        self.code, st = sp2_run(self.ctx)
+        self.stats = stats_dict(st)
+        return self.stats
+
+    def D_host(self):
+        return sp2_copy_D(self.ctx)
+
+    def D_device(self):
+        return device_view_to_torch(sp2_get_D(self.ctx))
+
+    def backward(self, W):
+        return device_view_to_torch(sp2_backward(self.ctx, W))
+
+    def close(self):
+        if self.ctx:
+            sp2_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def header_functions() -> list[str]:
+    """Names of the functions declared in include/sp2.h (for export checks)."""
+    import re
+    h = (Path(__file__).resolve().parent.parent / "include" / "sp2.h").read_text()
+    return sorted(set(re.findall(r"\b(sp2_[A-Za-z0-9_]+)\s*\(", h)))

@@ -1,0 +1,728 @@
+// C ABI (include/sp2.h) and the host side of the SP2ACC expansion:
+//   Section 4 Step 1 -- schedule (p_i, alpha_i, n_min, n_max, tau_i), Algorithm 1;
+//   Section 4 Step 2 -- Algorithm 2 (loop, stop test);
+//   Section 4 Step 3 -- homo/lumo estimates.
+// Every matrix operation is a kernel of this library on the caller's stream; the
+// host only sees scalars (tile counts, e_i, t_i, lambda bounds).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+#include <algorithm>
+
+#include "sp2_internal.h"
+
+using namespace sp2;
+
+namespace {
+
+constexpr double C_STOP = 6.8872;  // Algorithm 2
+
+// ------------------------------------------------------------------ schedule
+// Reading of Step 1 (the companion paper's Algorithm 4 is not reproduced in
+// the paper): eigenvalue images are tracked as intervals [vlo, vhi] (virtual,
+// near 0) and [olo, ohi] (occupied, near 1).  p = 1 (x^2) iff the virtual
+// interval is farther from 0 than the occupied one is from 1; while
+// acceleration is on, alpha folds the improved interval symmetrically about
+// the vertex of the polynomial (scale-and-fold); it switches off for good once
+// both distances are <= delta_acc.  Truncation with ||E||_2 <= tau widens both
+// intervals by tau (Weyl).  n_max: steps until both slack-free intervals are
+// within 2^-52 of {0, 1}.
+double poly_scalar(int p, double a, double x) {
+  if (p == 1) {
+    const double y = (1.0 - a) + a * x;
+    return y * y;
+  }
+  const double ax = a * x;
+  return (2.0 * a) * x - ax * ax;
+}
+
+void image(int p, double a, double& lo, double& hi) {
+  const double f1 = poly_scalar(p, a, lo), f2 = poly_scalar(p, a, hi);
+  double mn = std::min(f1, f2), mx = std::max(f1, f2);
+  const double vertex = (p == 1) ? (a - 1.0) / a : 1.0 / a;
+  if (lo <= vertex && vertex <= hi) {
+    const double fv = poly_scalar(p, a, vertex);
+    mn = std::min(mn, fv);
+    mx = std::max(mx, fv);
+  }
+  lo = mn;
+  hi = mx;
+}
+
+void choose(double vlo, double vhi, double olo, double ohi, bool& acc, double delta_acc, int& p, double& alpha) {
+  const double d0 = std::max(vhi, -vlo);
+  const double d1 = std::max(1.0 - olo, ohi - 1.0);
+  p = d0 > d1 ? 1 : 0;
+  if (acc && std::max(d0, d1) > delta_acc) {
+    alpha = (p == 1) ? 2.0 / ((2.0 - vlo) - vhi) : 2.0 / (olo + ohi);
+    alpha = std::max(alpha, 1.0);
+    return;
+  }
+  acc = false;
+  alpha = 1.0;
+}
+
+struct Schedule {
+  double lmin = 0, lmax = 0;
+  std::vector<int> p;
+  std::vector<double> alpha, tau, vhi, olo;
+  int n_min = 1, n_max = 0;
+};
+
+Schedule make_schedule(double lmin, double lmax, double homo_ub, double lumo_lb, double tau, double gamma,
+                       bool accelerate, double delta_acc, int n_cap) {
+  Schedule s;
+  s.lmin = lmin;
+  s.lmax = lmax;
+  const double w = lmax - lmin;
+  const double v0 = (lmax - lumo_lb) / w, o0 = (lmax - homo_ub) / w;
+  double vlo = 0.0, vhi = v0, olo = o0, ohi = 1.0;
+  bool acc = accelerate;
+  int n_max = n_cap;
+  for (int i = 1; i <= n_cap; ++i) {
+    int p;
+    double a;
+    choose(vlo, vhi, olo, ohi, acc, delta_acc, p, a);
+    image(p, a, vlo, vhi);
+    image(p, a, olo, ohi);
+    if (std::max(std::max(vhi, -vlo), std::max(1.0 - olo, ohi - 1.0)) < std::ldexp(1.0, -52)) {
+      n_max = i;
+      break;
+    }
+  }
+  s.n_max = n_max;
+  auto tau_of = [&](double vh, double ol) {
+    if (!(gamma > 0.0)) return tau;
+    const double g = gamma / (double)(n_max + 1);
+    return g * (ol - vh) / (1.0 + g);
+  };
+  vlo = 0.0; vhi = v0; olo = o0; ohi = 1.0;
+  double t0 = tau_of(vhi, olo);
+  s.tau.push_back(t0);
+  vlo -= t0; vhi += t0; olo -= t0; ohi += t0;
+  s.p.push_back(-1);
+  s.alpha.push_back(NAN);
+  s.vhi.push_back(vhi);
+  s.olo.push_back(olo);
+  acc = accelerate;
+  s.n_min = accelerate ? n_max + 1 : 1;
+  for (int i = 1; i <= n_max; ++i) {
+    int p;
+    double a;
+    const bool was = acc;
+    choose(vlo, vhi, olo, ohi, acc, delta_acc, p, a);
+    if (was && !acc) s.n_min = i;
+    s.p.push_back(p);
+    s.alpha.push_back(a);
+    image(p, a, vlo, vhi);
+    image(p, a, olo, ohi);
+    const double ti = tau_of(vhi, olo);
+    s.tau.push_back(ti);
+    vlo -= ti; vhi += ti; olo -= ti; ohi += ti;
+    s.vhi.push_back(vhi);
+    s.olo.push_back(olo);
+  }
+  return s;
+}
+
+void coeffs(int p, double a, double& c0, double& c1, double& c2) {
+  if (p == 1) {
+    c0 = (1.0 - a) * (1.0 - a);
+    c1 = 2.0 * a * (1.0 - a);
+    c2 = a * a;
+  } else {
+    c0 = 0.0;
+    c1 = 2.0 * a;
+    c2 = -(a * a);
+  }
+}
+
+// ------------------------------------------------------------------ Step 3
+// Reading of Step 3 (the interior-eigenvalue paper's Algorithm 3 is not
+// reproduced in the paper): every eigenvalue image x of X~_j adds r = x - x^2 to
+// t_j and r^2 to e_j^2.  A step with x^2 (p_j = 1) squares r on the virtual side
+// and about doubles it on the occupied side, so right after it the occupied side
+// carries e_j and t_j; after 2x - x^2 the virtual side does.  On that side the
+// largest r is estimated by e_j^2 / t_j, x = (1 +/- sqrt(1 - 4r)) / 2 next to the
+// gap, then x is pulled back through f_j..f_1 (gap-side branch) and X_0's map.
+// Per side the largest j with e_j > 100 f, t_j > 10 f, 10 f < r < 1/4 is used,
+// f = tau_j + sqrt(N) 2^-52.  Through scale-and-fold steps the gap-side branch
+// is an assumption (the fold maps two preimages onto one image).
+double pull_back(const Schedule& s, int j, double x) {
+  for (int i = j; i >= 1; --i) {
+    const int p = s.p[i];
+    const double a = s.alpha[i];
+    const double y = std::min(std::max(x, 0.0), 1.0);
+    if (p == 1) x = (std::sqrt(y) + a - 1.0) / a;
+    else x = (1.0 - std::sqrt(1.0 - y)) / a;
+  }
+  return s.lmax - x * (s.lmax - s.lmin);
+}
+
+void estimates(const Schedule& s, const std::vector<double>& e, const std::vector<double>& t, int64_t n,
+               double& homo, double& lumo, int& have) {
+  homo = lumo = NAN;
+  have = 0;
+  bool hf = false, lf = false;
+  for (int j = (int)t.size() - 1; j >= 1; --j) {
+    if (j >= (int)s.p.size()) continue;
+    const double f = s.tau[std::min<size_t>(j, s.tau.size() - 1)] + std::sqrt((double)n) * std::ldexp(1.0, -52);
+    if (!(e[j] > 100.0 * f && t[j] > 10.0 * f)) continue;
+    const double r = e[j] * e[j] / t[j];
+    if (!(10.0 * f < r && r < 0.25)) continue;
+    if (s.p[j] == 1 && !hf) {
+      homo = pull_back(s, j, (1.0 + std::sqrt(1.0 - 4.0 * r)) / 2.0);
+      hf = true;
+    } else if (s.p[j] == 0 && !lf) {
+      lumo = pull_back(s, j, (1.0 - std::sqrt(1.0 - 4.0 * r)) / 2.0);
+      lf = true;
+    }
+    if (hf && lf) break;
+  }
+  have = (hf ? 1 : 0) | (lf ? 2 : 0);
+}
+
+// ------------------------------------------------------------------ memory
+struct Alloc {
+  sp2_allocator a{};
+  bool custom = false;
+  cudaStream_t st = nullptr;
+  void* get(size_t bytes) {
+    if (bytes == 0) bytes = 256;
+    if (custom) return a.alloc(bytes, a.user);
+    void* p = nullptr;
+    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return p;
+  }
+  void put(void* p) {
+    if (!p) return;
+    if (custom) {
+      cudaStreamSynchronize(st);  // the caller's free is not stream-ordered
+      a.free(p, a.user);
+    } else {
+      cudaFreeAsync(p, st);
+    }
+  }
+};
+
+struct Buf {
+  void* p = nullptr;
+  size_t cap = 0;
+  template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+struct Fail {
+  int code;
+};
+
+}  // namespace
+
+struct sp2_ctx {
+  Alloc al;
+  cudaStream_t st = nullptr;
+  sp2_params prm{};
+  int64_t n = 0, nocc = 0;
+  int nb = 0, words = 0;
+  double homo_ub = 0, lumo_lb = 0, tau = 0;
+  Schedule sch;
+  std::vector<Buf*> bufs;
+  // F (kept for the adjoint) and X~ (current iterate, values in pool[cur])
+  TileSet F, X, out;
+  Buf f_brow, f_bcol, f_slot, f_rowptr, f_pool;
+  Buf x_brow, x_bcol, x_slot, x_rowptr;
+  Buf o_brow, o_bcol, o_slot, o_rowptr, o_bits;
+  Buf pool[2];
+  int cur = 0;
+  FullPattern fp;
+  Buf fp_bits, fp_rowptr, fp_col, fp_ref, counts;
+  Buf p_e2, p_trS, p_trX, p_n2, p_kt, keep, scanbuf, scantmp, twork, rowlo, rowhi;
+  Buf dsc, dcnt, d2;
+  StepScalars* h_sc = nullptr;
+  int32_t* h_cnt = nullptr;
+  double* h_d2 = nullptr;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr, evs0 = nullptr, evs1 = nullptr;
+  // outputs
+  Buf d_brow, d_bcol, d_val;
+  int64_t d_nnzb = 0;
+  bool ran = false, have_D = false;
+  sp2_stats stats{};
+  std::string last_error;
+
+  sp2_ctx() {
+    Buf* all[] = {&f_brow, &f_bcol, &f_slot, &f_rowptr, &f_pool, &x_brow, &x_bcol, &x_slot, &x_rowptr,
+                  &o_brow, &o_bcol, &o_slot, &o_rowptr, &o_bits, &pool[0], &pool[1], &fp_bits, &fp_rowptr,
+                  &fp_col, &fp_ref, &counts, &p_e2, &p_trS, &p_trX, &p_n2, &p_kt, &keep, &scanbuf, &scantmp,
+                  &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val};
+    for (Buf* b : all) bufs.push_back(b);
+  }
+
+  void ck(cudaError_t e, const char* what) {
+    if (e != cudaSuccess) {
+      last_error = std::string(what) + ": " + cudaGetErrorString(e);
+      throw Fail{SP2_ERR_CUDA};
+    }
+  }
+  void ensure(Buf& b, size_t bytes) {
+    if (b.cap >= bytes && b.p) return;
+    al.put(b.p);
+    b.p = nullptr;
+    b.cap = 0;
+    size_t want = std::max<size_t>(bytes + bytes / 4, 256);
+    b.p = al.get(want);
+    if (!b.p) {
+      last_error = "device allocation of " + std::to_string(want) + " bytes failed";
+      throw Fail{SP2_ERR_OOM};
+    }
+    b.cap = want;
+  }
+  void sync() { ck(cudaStreamSynchronize(st), "stream sync"); }
+};
+
+namespace {
+
+void set_tiles(TileSet& s, Buf& br, Buf& bc, Buf& sl, Buf& rp, int64_t nnzb) {
+  s.nnzb = nnzb;
+  s.brow = br.as<int32_t>();
+  s.bcol = bc.as<int32_t>();
+  s.slot = sl.as<int32_t>();
+  s.rowptr = rp.as<int32_t>();
+}
+
+// Both-triangle pattern of a tile set (bitmap + neighbour lists).
+void build_full(sp2_ctx* c, const TileSet& s, FullPattern& fp, Buf& bits, Buf& rowptr, Buf& col, Buf& ref) {
+  c->ensure(bits, (size_t)c->nb * c->words * 4);
+  c->ensure(rowptr, (size_t)(c->nb + 1) * 4);
+  c->ensure(col, (size_t)std::max<int64_t>(2 * s.nnzb, 1) * 4);
+  c->ensure(ref, (size_t)std::max<int64_t>(2 * s.nnzb, 1) * 4);
+  c->ensure(c->counts, (size_t)(c->nb + 1) * 4);
+  c->ensure(c->scantmp, scan_tmp_bytes(c->nb + 1) + scan_tmp_bytes(std::max<int64_t>(s.nnzb, c->nb)) + 4096);
+  fp.words = c->words;
+  fp.bits = bits.as<uint32_t>();
+  fp.rowptr = rowptr.as<int32_t>();
+  fp.col = col.as<int32_t>();
+  fp.ref = ref.as<uint32_t>();
+  fp.nnz = 2 * s.nnzb;
+  c->ck(launch_bitmap(s, c->nb, fp, c->st), "bitmap");
+  c->ck(launch_row_popc(fp.bits, c->nb, c->words, c->counts.as<int32_t>(), c->st), "row popc");
+  c->ck(launch_scan_i32(c->counts.as<int32_t>(), fp.rowptr, c->nb, fp.rowptr + c->nb, c->scantmp.p, c->st),
+        "scan");
+  c->ck(launch_fill_full(s, c->nb, fp, c->st), "fill full");
+}
+
+void ensure_partials(sp2_ctx* c, int64_t nt) {
+  const size_t d = (size_t)std::max<int64_t>(nt, 1) * 8, i4 = (size_t)std::max<int64_t>(nt, 1) * 4;
+  c->ensure(c->p_e2, d);
+  c->ensure(c->p_trS, d);
+  c->ensure(c->p_trX, d);
+  c->ensure(c->p_n2, d);
+  c->ensure(c->p_kt, i4);
+  c->ensure(c->keep, i4);
+  c->ensure(c->scanbuf, i4);
+}
+
+Partials partials(sp2_ctx* c) {
+  Partials p;
+  p.e2 = c->p_e2.as<double>();
+  p.trS = c->p_trS.as<double>();
+  p.trX = c->p_trX.as<double>();
+  p.n2 = c->p_n2.as<double>();
+  p.ktiles = c->p_kt.as<int32_t>();
+  return p;
+}
+
+int32_t read_count(sp2_ctx* c, const int32_t* dev) {
+  c->ck(cudaMemcpyAsync(c->h_cnt, dev, sizeof(int32_t), cudaMemcpyDeviceToHost, c->st), "count d2h");
+  c->sync();
+  return *c->h_cnt;
+}
+
+// Truncate the tile set `in` (values indexed by slot, norms in n2[slot]) and
+// compact its index into the X buffers.
+void truncate_into_X(sp2_ctx* c, const TileSet& in, const double* n2, double tau) {
+  const int64_t part_tiles = std::max<int64_t>(1, c->prm.frobinf_part / TB);
+  // n2 may live in p_n2: only the flag buffers are (re)sized here
+  c->ensure(c->keep, (size_t)std::max<int64_t>(in.nnzb, 1) * 4);
+  c->ensure(c->scanbuf, (size_t)std::max<int64_t>(in.nnzb, 1) * 4);
+  c->ensure(c->twork, trunc_work_bytes(std::max<int64_t>(in.nnzb, 1), c->nb, part_tiles));
+  c->ck(launch_truncate(in, n2, c->nb, tau, c->prm.trunc, part_tiles, c->twork.p, c->keep.as<int32_t>(), c->st),
+        "truncate");
+  const size_t cap = (size_t)std::max<int64_t>(in.nnzb, 1) * 4;
+  c->ensure(c->x_brow, cap);
+  c->ensure(c->x_bcol, cap);
+  c->ensure(c->x_slot, cap);
+  c->ensure(c->x_rowptr, (size_t)(c->nb + 1) * 4);
+  c->ensure(c->dcnt, 16);
+  c->ensure(c->scantmp, scan_tmp_bytes(in.nnzb) + 4096);
+  set_tiles(c->X, c->x_brow, c->x_bcol, c->x_slot, c->x_rowptr, 0);
+  c->ck(launch_compact(in, c->keep.as<int32_t>(), c->nb, c->X, c->dcnt.as<int32_t>(), c->scantmp.p,
+                       c->scanbuf.as<int32_t>(), c->st),
+        "compact");
+  c->X.nnzb = read_count(c, c->dcnt.as<int32_t>());
+  c->ck(launch_rowptr_from_brow(c->X.brow, c->X.nnzb, c->nb, c->X.rowptr, c->st), "rowptr");
+}
+
+int fill_stats_sched(sp2_ctx* c) {
+  sp2_stats& s = c->stats;
+  s.n_min = c->sch.n_min;
+  s.n_max = c->sch.n_max;
+  s.lmin = c->sch.lmin;
+  s.lmax = c->sch.lmax;
+  for (int i = 0; i < SP2_MAX_ITER; ++i) {
+    s.p[i] = i < (int)c->sch.p.size() ? c->sch.p[i] : -1;
+    s.alpha[i] = i < (int)c->sch.alpha.size() ? c->sch.alpha[i] : NAN;
+    s.tau[i] = i < (int)c->sch.tau.size() ? c->sch.tau[i] : NAN;
+  }
+  return 0;
+}
+
+int guard(sp2_ctx* c, int code) {
+  if (c) c->stats.status = code;
+  return code;
+}
+
+}  // namespace
+
+// ====================================================================== C ABI
+extern "C" {
+
+int sp2_default_params(sp2_params* p) {
+  if (!p) return SP2_ERR_INVALID_ARG;
+  std::memset(p, 0, sizeof(*p));
+  p->mode = SP2_MODE_SP2ACC;
+  p->stop = SP2_STOP_PARAMETERLESS;
+  p->idem_tol = 1e-12;
+  p->trunc = SP2_TRUNC_FROBENIUS;
+  p->frobinf_part = 4096;
+  p->gamma = 0.0;
+  p->delta_acc = 0.1;
+  p->n_max_cap = 100;
+  p->precision = SP2_PREC_FP64;
+  p->slices = 4;
+  p->mixed_from = 1;
+  p->mixed_until = 0;
+  p->ckpt_every = 8;
+  p->record_masks = 1;
+  return SP2_OK;
+}
+
+const char* sp2_strerror(int code) {
+  switch (code) {
+    case SP2_OK: return "ok";
+    case SP2_ERR_INVALID_ARG: return "invalid argument";
+    case SP2_ERR_BOUNDS: return "invalid homo/lumo bounds";
+    case SP2_ERR_PATTERN: return "invalid tile pattern";
+    case SP2_ERR_NONFINITE: return "non-finite value in input";
+    case SP2_ERR_OOM: return "device allocation failed";
+    case SP2_ERR_CUDA: return "CUDA error";
+    case SP2_ERR_NOT_CONVERGED: return "not converged within n_max iterations";
+    case SP2_ERR_TIMEOUT: return "bounded device wait timed out";
+    case SP2_ERR_STATE: return "call out of order";
+    case SP2_ERR_CAPACITY: return "buffer too small";
+    default: return "unknown error";
+  }
+}
+
+int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, double tau,
+               const sp2_params* params, const sp2_allocator* alloc, void* cuda_stream, sp2_ctx** out) {
+  if (!out) return SP2_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!F || F->b != TB || F->n <= 0 || F->nnzb <= 0 || !F->brow || !F->bcol || !F->val) return SP2_ERR_INVALID_ARG;
+  if (!std::isfinite(homo_ub) || !std::isfinite(lumo_lb) || !std::isfinite(tau) || tau < 0.0)
+    return SP2_ERR_INVALID_ARG;
+  if (!(homo_ub < lumo_lb)) return SP2_ERR_BOUNDS;
+  if (alloc && (!alloc->alloc || !alloc->free)) return SP2_ERR_INVALID_ARG;
+  sp2_params prm;
+  sp2_default_params(&prm);
+  if (params) prm = *params;
+  if (prm.mode != SP2_MODE_SP2 && prm.mode != SP2_MODE_SP2ACC) return SP2_ERR_INVALID_ARG;
+  if (prm.stop != SP2_STOP_PARAMETERLESS && prm.stop != SP2_STOP_IDEMPOTENCY) return SP2_ERR_INVALID_ARG;
+  if (prm.trunc != SP2_TRUNC_FROBENIUS && prm.trunc != SP2_TRUNC_FROBINF) return SP2_ERR_INVALID_ARG;
+  if (prm.trunc == SP2_TRUNC_FROBINF && (prm.frobinf_part < TB || prm.frobinf_part % TB)) return SP2_ERR_INVALID_ARG;
+  if (prm.n_max_cap < 1 || prm.n_max_cap > SP2_MAX_ITER - 2) return SP2_ERR_INVALID_ARG;
+  if (prm.precision != SP2_PREC_FP64 && prm.precision != SP2_PREC_SPLIT16) return SP2_ERR_INVALID_ARG;
+  if (prm.precision == SP2_PREC_SPLIT16 && (prm.slices < 2 || prm.slices > 4)) return SP2_ERR_INVALID_ARG;
+  if (prm.ckpt_every < 1) return SP2_ERR_INVALID_ARG;
+  const int64_t nb64 = (F->n + TB - 1) / TB;
+  if (nb64 > 65535) return SP2_ERR_INVALID_ARG;
+
+  sp2_ctx* c = new (std::nothrow) sp2_ctx();
+  if (!c) return SP2_ERR_OOM;
+  c->st = static_cast<cudaStream_t>(cuda_stream);
+  c->al.st = c->st;
+  if (alloc) {
+    c->al.a = *alloc;
+    c->al.custom = true;
+  }
+  c->prm = prm;
+  c->n = F->n;
+  c->nb = (int)nb64;
+  c->words = (c->nb + 31) / 32;
+  c->nocc = nocc;
+  c->homo_ub = homo_ub;
+  c->lumo_lb = lumo_lb;
+  c->tau = tau;
+  try {
+    c->ck(cudaEventCreate(&c->ev0), "event");
+    c->ck(cudaEventCreate(&c->ev1), "event");
+    c->ck(cudaEventCreate(&c->evs0), "event");
+    c->ck(cudaEventCreate(&c->evs1), "event");
+    c->ck(cudaMallocHost(&c->h_sc, sizeof(StepScalars)), "host alloc");
+    c->ck(cudaMallocHost(&c->h_cnt, 16), "host alloc");
+    c->ck(cudaMallocHost(&c->h_d2, 16), "host alloc");
+    const int64_t nnzb = F->nnzb;
+    const cudaMemcpyKind kind = F->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    c->ensure(c->f_brow, nnzb * 4);
+    c->ensure(c->f_bcol, nnzb * 4);
+    c->ensure(c->f_slot, nnzb * 4);
+    c->ensure(c->f_rowptr, (c->nb + 1) * 4);
+    c->ensure(c->f_pool, (size_t)nnzb * TE * 8);
+    c->ck(cudaMemcpyAsync(c->f_brow.p, F->brow, nnzb * 4, kind, c->st), "copy F");
+    c->ck(cudaMemcpyAsync(c->f_bcol.p, F->bcol, nnzb * 4, kind, c->st), "copy F");
+    c->ck(cudaMemcpyAsync(c->f_pool.p, F->val, (size_t)nnzb * TE * 8, kind, c->st), "copy F");
+    // validation: sorted upper pattern, every diagonal tile, finite values
+    c->ensure(c->dcnt, 16);
+    c->ck(launch_check_pattern(c->f_brow.as<int32_t>(), c->f_bcol.as<int32_t>(), nnzb, c->nb, c->f_pool.as<double>(),
+                               c->n, c->dcnt.as<int32_t>(), c->st),
+          "check");
+    c->ck(cudaMemcpyAsync(c->h_cnt, c->dcnt.p, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
+    c->sync();
+    if (c->h_cnt[0] & 1) throw Fail{SP2_ERR_PATTERN};
+    if (c->h_cnt[1] != c->nb) throw Fail{SP2_ERR_PATTERN};
+    if (c->h_cnt[0] & 2) throw Fail{SP2_ERR_NONFINITE};
+    // slots of F are the identity
+    {
+      std::vector<int32_t> id(nnzb);
+      for (int64_t i = 0; i < nnzb; ++i) id[i] = (int32_t)i;
+      c->ck(cudaMemcpyAsync(c->f_slot.p, id.data(), nnzb * 4, cudaMemcpyHostToDevice, c->st), "slots");
+      c->sync();
+    }
+    set_tiles(c->F, c->f_brow, c->f_bcol, c->f_slot, c->f_rowptr, nnzb);
+    c->ck(launch_rowptr_from_brow(c->F.brow, nnzb, c->nb, c->F.rowptr, c->st), "rowptr");
+    // Gershgorin (Section 4, Step 1)
+    build_full(c, c->F, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
+    c->ensure(c->rowlo, c->n * 8);
+    c->ensure(c->rowhi, c->n * 8);
+    c->ensure(c->d2, 16);
+    c->ck(launch_gershgorin(c->fp, c->f_pool.as<double>(), c->nb, c->n, c->rowlo.as<double>(), c->rowhi.as<double>(),
+                            c->st),
+          "gershgorin");
+    c->ck(launch_minmax(c->rowlo.as<double>(), c->rowhi.as<double>(), c->n, c->d2.as<double>(), c->st), "minmax");
+    c->ck(cudaMemcpyAsync(c->h_d2, c->d2.p, 16, cudaMemcpyDeviceToHost, c->st), "d2h");
+    c->sync();
+    const double lmin = c->h_d2[0], lmax = c->h_d2[1];
+    if (!(lmin <= homo_ub) || !(lumo_lb <= lmax) || !(lmax > lmin)) throw Fail{SP2_ERR_BOUNDS};
+    c->sch = make_schedule(lmin, lmax, homo_ub, lumo_lb, tau, prm.gamma, prm.mode == SP2_MODE_SP2ACC, prm.delta_acc,
+                           prm.n_max_cap);
+    fill_stats_sched(c);
+    c->stats.status = SP2_OK;
+    c->stats.homo_est = c->stats.lumo_est = NAN;
+  } catch (const Fail& f) {
+    if (f.code == SP2_ERR_CUDA || f.code == SP2_ERR_OOM) fprintf(stderr, "sp2_create: %s\n", c->last_error.c_str());
+    sp2_destroy(c);
+    return f.code;
+  }
+  *out = c;
+  return SP2_OK;
+}
+
+int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
+  if (!c) return SP2_ERR_INVALID_ARG;
+  int status = SP2_OK;
+  try {
+    sp2_stats& S = c->stats;
+    const Schedule& sch = c->sch;
+    fill_stats_sched(c);
+    S.converged = 0;
+    S.squares = 0;
+    S.tile_triplets = 0;
+    S.square_ms = 0.0;
+    S.have_estimates = 0;
+    S.homo_est = S.lumo_est = NAN;
+    for (int i = 0; i < SP2_MAX_ITER; ++i) {
+      S.e[i] = S.t[i] = NAN;
+      S.nnzb_hist[i] = -1;
+      S.prec_hist[i] = -1;
+    }
+    c->ck(cudaEventRecord(c->ev0, c->st), "event");
+    // Algorithm 1: X_0 on F's pattern, then X~_0 = trunc(X_0, tau_0)
+    const int64_t nF = c->F.nnzb;
+    c->ensure(c->pool[0], (size_t)nF * TE * 8);
+    ensure_partials(c, nF);
+    c->ck(launch_x0(c->F, c->f_pool.as<double>(), c->pool[0].as<double>(), c->n, sch.lmax, sch.lmax - sch.lmin,
+                    c->p_n2.as<double>(), c->st),
+          "x0");
+    c->cur = 0;
+    truncate_into_X(c, c->F, c->p_n2.as<double>(), sch.tau[0]);
+    S.nnzb_hist[0] = c->X.nnzb;
+    std::vector<double> ev, tv;
+    int n_out = -1;
+    bool converged = false;
+    for (int i = 1; i <= sch.n_max + 1; ++i) {
+      // symbolic: both-triangle pattern of X~_{i-1}, product pattern (upper + diagonal)
+      build_full(c, c->X, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
+      c->ensure(c->o_bits, (size_t)c->nb * c->words * 4);
+      c->ensure(c->o_rowptr, (size_t)(c->nb + 1) * 4);
+      c->ck(launch_product_bits(c->fp, c->fp, c->nb, c->o_bits.as<uint32_t>(), c->st), "product bits");
+      c->ck(launch_row_popc(c->o_bits.as<uint32_t>(), c->nb, c->words, c->counts.as<int32_t>(), c->st), "popc");
+      c->ck(launch_scan_i32(c->counts.as<int32_t>(), c->o_rowptr.as<int32_t>(), c->nb,
+                            c->o_rowptr.as<int32_t>() + c->nb, c->scantmp.p, c->st),
+            "scan");
+      const int64_t nout = read_count(c, c->o_rowptr.as<int32_t>() + c->nb);
+      c->ensure(c->o_brow, nout * 4);
+      c->ensure(c->o_bcol, nout * 4);
+      c->ensure(c->o_slot, nout * 4);
+      set_tiles(c->out, c->o_brow, c->o_bcol, c->o_slot, c->o_rowptr, nout);
+      c->ck(launch_fill_upper_from_bits(c->o_bits.as<uint32_t>(), c->nb, c->words, c->out.rowptr, c->out.brow,
+                                        c->out.bcol, c->out.slot, c->st),
+            "fill upper");
+      const int nxt = 1 - c->cur;
+      c->ensure(c->pool[nxt], (size_t)nout * TE * 8);
+      ensure_partials(c, nout);
+      int p = 1;
+      double a = 1.0;
+      if (i <= sch.n_max) { p = sch.p[i]; a = sch.alpha[i]; }
+      double c0, c1, c2;
+      coeffs(p, a, c0, c1, c2);
+      SquareArgs sa;
+      sa.A = &c->fp; sa.apool = c->pool[c->cur].as<double>();
+      sa.B = &c->fp; sa.bpool = sa.apool;
+      sa.sym_sum = false;
+      sa.Z = &c->fp; sa.zpool = sa.apool;
+      sa.out = &c->out; sa.outpool = c->pool[nxt].as<double>();
+      sa.c0 = c0; sa.c1 = c1; sa.c2 = c2;
+      sa.n = c->n; sa.nb = c->nb;
+      sa.part = partials(c);
+      c->ck(cudaEventRecord(c->evs0, c->st), "event");
+      c->ck(launch_square_f64(sa, c->st), "square f64");
+      c->ck(cudaEventRecord(c->evs1, c->st), "event");
+      c->ensure(c->dsc, sizeof(StepScalars));
+      c->ck(launch_reduce_step(sa.part, nout, c->dsc.as<StepScalars>(), c->st), "reduce");
+      c->ck(cudaMemcpyAsync(c->h_sc, c->dsc.p, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->st), "d2h");
+      c->sync();
+      float ms = 0.f;
+      c->ck(cudaEventElapsedTime(&ms, c->evs0, c->evs1), "elapsed");
+      S.square_ms += ms;
+      S.squares += 1;
+      S.tile_triplets += c->h_sc->triplets;
+      const int j = i - 1;
+      const double ej = std::sqrt(std::max(c->h_sc->e2, 0.0));
+      const double tj = c->h_sc->trX - c->h_sc->trS;
+      ev.push_back(ej);
+      tv.push_back(tj);
+      S.e[j] = ej;
+      S.t[j] = tj;
+      S.prec_hist[j] = SP2_PREC_FP64;
+      bool stop = false;
+      if (c->prm.stop == SP2_STOP_PARAMETERLESS) {
+        stop = j >= std::max(sch.n_min, 2) && sch.p[j] != sch.p[j - 1] && ev[j] > C_STOP * (ev[j - 2] * ev[j - 2]);
+      } else {
+        stop = ev[j] < c->prm.idem_tol;
+      }
+      if (stop) { n_out = j; converged = true; break; }
+      if (i == sch.n_max + 1) { n_out = j; break; }
+      // X~_i = trunc(X_i, tau_i); X_i's tiles live in pool[nxt] at slot = output index
+      truncate_into_X(c, c->out, c->p_n2.as<double>(), sch.tau[i]);
+      c->cur = nxt;
+      S.nnzb_hist[i] = c->X.nnzb;
+    }
+    // D = X~_n: contiguous copy for the caller's view
+    c->d_nnzb = c->X.nnzb;
+    c->ensure(c->d_brow, std::max<int64_t>(c->d_nnzb, 1) * 4);
+    c->ensure(c->d_bcol, std::max<int64_t>(c->d_nnzb, 1) * 4);
+    c->ensure(c->d_val, (size_t)std::max<int64_t>(c->d_nnzb, 1) * TE * 8);
+    c->ck(launch_copy_index(c->X, c->d_brow.as<int32_t>(), c->d_bcol.as<int32_t>(), c->st), "copy index");
+    c->ck(launch_gather_tiles(c->X, c->pool[c->cur].as<double>(), c->d_val.as<double>(), c->st), "gather");
+    c->ck(cudaEventRecord(c->ev1, c->st), "event");
+    c->sync();
+    float ms = 0.f;
+    c->ck(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "elapsed");
+    S.run_ms = ms;
+    S.n = n_out;
+    S.converged = converged ? 1 : 0;
+    S.nnzb_final = c->d_nnzb;
+    S.alg_flops = 2.0 * TB * TB * TB * (double)S.tile_triplets;
+    double h = NAN, l = NAN;
+    int have = 0;
+    estimates(sch, ev, tv, c->n, h, l, have);
+    S.homo_est = h;
+    S.lumo_est = l;
+    S.have_estimates = have;
+    c->ran = true;
+    c->have_D = true;
+    status = converged ? SP2_OK : SP2_ERR_NOT_CONVERGED;
+  } catch (const Fail& f) {
+    if (f.code == SP2_ERR_CUDA || f.code == SP2_ERR_OOM) fprintf(stderr, "sp2_run: %s\n", c->last_error.c_str());
+    status = f.code;
+  }
+  c->stats.status = status;
+  if (stats_out) *stats_out = c->stats;
+  return status;
+}
+
+int sp2_get_D(sp2_ctx* c, sp2_bsr* view) {
+  if (!c || !view) return SP2_ERR_INVALID_ARG;
+  if (!c->have_D) return SP2_ERR_STATE;
+  view->n = c->n;
+  view->b = TB;
+  view->nnzb = c->d_nnzb;
+  view->brow = c->d_brow.as<int32_t>();
+  view->bcol = c->d_bcol.as<int32_t>();
+  view->val = c->d_val.as<double>();
+  view->on_device = 1;
+  return SP2_OK;
+}
+
+int sp2_copy_D(sp2_ctx* c, int32_t* brow, int32_t* bcol, double* val, int64_t cap_nnzb, int32_t on_device,
+               int64_t* nnzb_out) {
+  if (!c) return SP2_ERR_INVALID_ARG;
+  if (!c->have_D) return SP2_ERR_STATE;
+  if (nnzb_out) *nnzb_out = c->d_nnzb;
+  if (cap_nnzb < c->d_nnzb) return SP2_ERR_CAPACITY;
+  if (!brow || !bcol || !val) return SP2_ERR_INVALID_ARG;
+  const cudaMemcpyKind k = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+  try {
+    c->ck(cudaMemcpyAsync(brow, c->d_brow.p, c->d_nnzb * 4, k, c->st), "copy D");
+    c->ck(cudaMemcpyAsync(bcol, c->d_bcol.p, c->d_nnzb * 4, k, c->st), "copy D");
+    c->ck(cudaMemcpyAsync(val, c->d_val.p, (size_t)c->d_nnzb * TE * 8, k, c->st), "copy D");
+    c->sync();
+  } catch (const Fail& f) {
+    return f.code;
+  }
+  return SP2_OK;
+}
+
+int sp2_backward(sp2_ctx* c, const sp2_bsr* W, sp2_bsr* dF) {
+  if (!c || !W || !dF) return SP2_ERR_INVALID_ARG;
+  return SP2_ERR_STATE;
+}
+
+int sp2_get_stats(const sp2_ctx* c, sp2_stats* s) {
+  if (!c || !s) return SP2_ERR_INVALID_ARG;
+  *s = c->stats;
+  return SP2_OK;
+}
+
+void sp2_destroy(sp2_ctx* c) {
+  if (!c) return;
+  for (Buf* b : c->bufs) {
+    c->al.put(b->p);
+    b->p = nullptr;
+  }
+  cudaStreamSynchronize(c->st);
+  if (c->h_sc) cudaFreeHost(c->h_sc);
+  if (c->h_cnt) cudaFreeHost(c->h_cnt);
+  if (c->h_d2) cudaFreeHost(c->h_d2);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->evs0) cudaEventDestroy(c->evs0);
+  if (c->evs1) cudaEventDestroy(c->evs1);
+  delete c;
+}
+
+}  // extern "C"

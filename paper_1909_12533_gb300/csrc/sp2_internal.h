@@ -1,0 +1,110 @@
+// Internal declarations of the SP2 library: device data layout and kernel
+// launchers.  Everything here is private to the shared library; the public
+// boundary is include/sp2.h.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <cstddef>
+#include "sp2.h"
+
+namespace sp2 {
+
+constexpr int TB = 32;          // tile edge (Section 6: small block size 32)
+constexpr int TE = TB * TB;     // elements per tile
+
+// A set of upper-triangle tiles (I <= J), sorted by (I, J).  Tile t's values
+// live in a value pool at pool[slot[t] * TE .. + TE), row-major.
+struct TileSet {
+  int64_t nnzb = 0;
+  int32_t* brow = nullptr;
+  int32_t* bcol = nullptr;
+  int32_t* slot = nullptr;
+  int32_t* rowptr = nullptr;    // [nb + 1] offsets of each tile row
+};
+
+// Both-triangle view of a symmetric tile pattern, used by the products.
+//  bits:  nb x words bitmap, bit K of row R set iff tile (R, K) or (K, R) is stored.
+//  rowptr/col/ref: for row R, the stored neighbours K in ascending order; ref =
+//  slot | (1u << 31) when X_RK is the transpose of the stored tile (K, R).
+struct FullPattern {
+  int32_t words = 0;
+  uint32_t* bits = nullptr;
+  int32_t* rowptr = nullptr;    // [nb + 1]
+  int32_t* col = nullptr;       // [nnz]
+  uint32_t* ref = nullptr;      // [nnz]
+  int64_t nnz = 0;
+};
+
+constexpr uint32_t REF_T = 0x80000000u;
+
+// Per-output-tile partial sums written by the fused epilogue.
+struct Partials {
+  double* e2 = nullptr;       // w * ||X~_IJ - S_IJ||_F^2  (w = 2 off the diagonal)
+  double* trS = nullptr;      // trace part of S on diagonal tiles
+  double* trX = nullptr;      // trace part of X~ on diagonal tiles
+  double* n2 = nullptr;       // ||X_new tile||_F^2
+  int32_t* ktiles = nullptr;  // number of K tiles that contributed
+};
+
+// Scalars of one fused step, reduced in a fixed order.
+struct StepScalars {
+  double e2, trS, trX, pad;
+  long long triplets;
+  long long pad2[3];
+};
+
+// ---------------------------------------------------------------- launchers
+// pattern.cu
+cudaError_t launch_bitmap(const TileSet& s, int nb, FullPattern& fp, cudaStream_t st);
+cudaError_t launch_row_popc(const uint32_t* bits, int nb, int words, int32_t* counts, cudaStream_t st);
+cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t n, int32_t* total_dev,
+                            void* tmp, cudaStream_t st);
+size_t scan_tmp_bytes(int64_t n);
+cudaError_t launch_fill_full(const TileSet& s, int nb, FullPattern& fp, cudaStream_t st);
+cudaError_t launch_product_bits(const FullPattern& a, const FullPattern& b, int nb, uint32_t* out_bits,
+                                cudaStream_t st);
+cudaError_t launch_fill_upper_from_bits(const uint32_t* bits, int nb, int words, const int32_t* rowptr,
+                                        int32_t* brow, int32_t* bcol, int32_t* slot, cudaStream_t st);
+cudaError_t launch_rowptr_from_brow(const int32_t* brow, int64_t nnzb, int nb, int32_t* rowptr,
+                                    cudaStream_t st);
+cudaError_t launch_check_pattern(const int32_t* brow, const int32_t* bcol, int64_t nnzb, int nb,
+                                 const double* val, int64_t n, int32_t* flag, cudaStream_t st);
+
+// init.cu
+cudaError_t launch_gershgorin(const FullPattern& fp, const double* pool, int nb, int64_t n, double* rowlo,
+                              double* rowhi, cudaStream_t st);
+cudaError_t launch_minmax(const double* lo, const double* hi, int64_t n, double* out2, cudaStream_t st);
+cudaError_t launch_x0(const TileSet& f, const double* fpool, double* xpool, int64_t n, double lmax, double w,
+                      double* n2, cudaStream_t st);
+
+// square_f64.cu: X_new = c0 I + c1 Z + c2 * (A B  [+ B A])  on the tiles of `out`
+struct SquareArgs {
+  const FullPattern* A;  const double* apool;
+  const FullPattern* B;  const double* bpool;   // B == A for the forward square
+  bool sym_sum;                                 // add B A too (adjoint)
+  const FullPattern* Z;  const double* zpool;   // tile (I, J) of Z (may be absent -> 0)
+  const TileSet* out; double* outpool;
+  double c0, c1, c2;
+  int64_t n; int nb;
+  Partials part;
+};
+cudaError_t launch_square_f64(const SquareArgs& a, cudaStream_t st);
+cudaError_t launch_reduce_step(const Partials& p, int64_t ntiles, StepScalars* out, cudaStream_t st);
+
+// trunc.cu: choose the tiles to drop (Frobenius / Frob-Inf readings)
+struct TruncWork;
+size_t trunc_work_bytes(int64_t nnzb, int nb, int64_t part_tiles);
+cudaError_t launch_truncate(const TileSet& x, const double* n2, int nb, double tau, int mode, int64_t part_tiles,
+                            void* work, int32_t* keep, cudaStream_t st);
+
+// compact.cu
+cudaError_t launch_compact(const TileSet& in, const int32_t* keep, int nb, TileSet& out, int32_t* count_dev,
+                           void* scan_tmp, int32_t* scan_buf, cudaStream_t st);
+cudaError_t launch_gather_tiles(const TileSet& s, const double* pool, double* dst, cudaStream_t st);
+cudaError_t launch_copy_index(const TileSet& s, int32_t* brow, int32_t* bcol, cudaStream_t st);
+cudaError_t launch_mask_to_pattern(const TileSet& src, const double* srcpool, const FullPattern& dstpat,
+                                   const TileSet& dst, double* dstpool, double scale, cudaStream_t st);
+cudaError_t launch_sym_into(const TileSet& w, const double* wpool, const FullPattern& pat, const TileSet& dst,
+                            double* dstpool, cudaStream_t st);
+
+}  // namespace sp2

@@ -1,0 +1,258 @@
+// Truncation X~_i = X_i + E_i with ||E_i|| <= tau_i (Section 2, Eqs. (6)-(8)).
+//
+// Selection rule (the paper states only the bound, so this is a reading):
+//  - Frobenius mode: sort the tiles by (||X_IJ||_F^2, I * nb + J) ascending and drop
+//    the longest prefix whose weighted squared norms fit into tau^2; weight 2 for
+//    off-diagonal tiles (their mirror is dropped too), 1 for diagonal tiles.
+//  - Frob-Inf mode (Section 3, Eq. (13), square partition of `part` rows): every
+//    super-block (R, C) gets the budget tau / max(m_R, m_C), m_R = number of
+//    nonzero super-blocks in super-row R; the Frobenius rule runs inside each
+//    super-block (weight 2 only for off-diagonal tiles of diagonal super-blocks).
+//    Then every super-row sum of ||E_RC||_F is <= tau, so ||E||_2 <= ||E||_M <= tau.
+//  - Sums are taken in integer units of budget * 2^-36 with each tile's share
+//    rounded up, so they are exact, independent of summation order, and never
+//    understate ||E||_F^2.
+//
+// GPU form: a segmented most-significant-digit radix select over the 96-bit key
+// (63 bits of the squared norm's IEEE pattern -- non-negative doubles order like
+// their bit patterns -- then the 32-bit linear tile index).  Twelve passes of
+// 8 bits; each pass histograms the budget units of the remaining candidates and
+// one thread per segment walks its 256 buckets.  No sort, no host round trip.
+#include "sp2_internal.h"
+
+namespace sp2 {
+namespace {
+
+constexpr double Q_SCALE = 68719476736.0;          // 2^36
+constexpr unsigned long long Q_BUDGET = 1ull << 36;
+constexpr unsigned long long Q_CAP = 1ull << 37;
+
+struct Work {
+  unsigned long long* q;
+  int32_t* seg;
+  double* scale;
+  unsigned long long* rem;
+  unsigned long long* pref_hi;
+  uint32_t* pref_lo;
+  int32_t* state;
+  int32_t* depth;
+  unsigned long long* hist;
+  int32_t* nz;
+  int32_t* m;
+  int64_t nseg;
+  int32_t nsb;
+};
+
+inline size_t align_up(size_t x) { return (x + 255) & ~size_t(255); }
+
+Work carve(void* base, int64_t nnzb, int64_t nseg, int nsb) {
+  char* p = static_cast<char*>(base);
+  Work w;
+  w.q = reinterpret_cast<unsigned long long*>(p); p += align_up(nnzb * 8);
+  w.seg = reinterpret_cast<int32_t*>(p); p += align_up(nnzb * 4);
+  w.scale = reinterpret_cast<double*>(p); p += align_up(nseg * 8);
+  w.rem = reinterpret_cast<unsigned long long*>(p); p += align_up(nseg * 8);
+  w.pref_hi = reinterpret_cast<unsigned long long*>(p); p += align_up(nseg * 8);
+  w.pref_lo = reinterpret_cast<uint32_t*>(p); p += align_up(nseg * 4);
+  w.state = reinterpret_cast<int32_t*>(p); p += align_up(nseg * 4);
+  w.depth = reinterpret_cast<int32_t*>(p); p += align_up(nseg * 4);
+  w.hist = reinterpret_cast<unsigned long long*>(p); p += align_up(nseg * 256 * 8);
+  w.nz = reinterpret_cast<int32_t*>(p); p += align_up((size_t)nsb * nsb * 4);
+  w.m = reinterpret_cast<int32_t*>(p); p += align_up((size_t)nsb * 4);
+  w.nseg = nseg;
+  w.nsb = nsb;
+  return w;
+}
+
+__global__ void k_nz(const int32_t* __restrict__ brow, const int32_t* __restrict__ bcol, int64_t nnzb, int pt,
+                     int nsb, int32_t* nz) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnzb) return;
+  const int R = brow[t] / pt, C = bcol[t] / pt;
+  nz[R * nsb + C] = 1;
+  nz[C * nsb + R] = 1;
+}
+
+__global__ void k_m(const int32_t* __restrict__ nz, int nsb, int32_t* m) {
+  const int R = blockIdx.x * blockDim.x + threadIdx.x;
+  if (R >= nsb) return;
+  int c = 0;
+  for (int C = 0; C < nsb; ++C) c += nz[R * nsb + C];
+  m[R] = c;
+}
+
+// mode 0: one segment, budget tau^2.  mode 1: segment R * nsb + C.
+__global__ void k_seg_init(Work w, int mode, double tau) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= w.nseg) return;
+  double budget;
+  if (mode == 0) {
+    budget = tau * tau;
+  } else {
+    const int R = (int)(s / w.nsb), C = (int)(s % w.nsb);
+    const int mm = max(w.m[R], w.m[C]);
+    const double beta = mm > 0 ? tau / (double)mm : 0.0;
+    budget = beta * beta;
+  }
+  w.scale[s] = budget > 0.0 ? Q_SCALE / budget : 0.0;
+  w.rem[s] = Q_BUDGET;
+  w.pref_hi[s] = 0ull;
+  w.pref_lo[s] = 0u;
+  w.state[s] = 0;
+  w.depth[s] = 0;
+}
+
+__global__ void k_q(const int32_t* __restrict__ brow, const int32_t* __restrict__ bcol,
+                    const int32_t* __restrict__ slot, const double* __restrict__ n2, int64_t nnzb, int mode, int pt,
+                    Work w) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnzb) return;
+  const int I = brow[t], J = bcol[t];
+  int s = 0;
+  double wt = (I == J) ? 1.0 : 2.0;
+  if (mode == 1) {
+    const int R = I / pt, C = J / pt;
+    s = R * w.nsb + C;
+    if (R != C) wt = 1.0;
+  }
+  w.seg[t] = s;
+  const double v = n2[slot ? slot[t] : t];
+  const double sc = w.scale[s];
+  unsigned long long q;
+  if (sc == 0.0) {
+    q = (v == 0.0) ? 0ull : Q_CAP;
+  } else {
+    const double x = (wt * v) * sc;
+    q = (x >= (double)Q_CAP) ? Q_CAP : (unsigned long long)ceil(x);
+  }
+  w.q[t] = q;
+}
+
+__device__ __forceinline__ bool is_candidate(unsigned long long hi, uint32_t lo, int p, unsigned long long ph,
+                                             uint32_t pl) {
+  if (p == 0) return true;
+  if (p <= 8) return (hi >> (64 - 8 * p)) == ph;
+  return hi == ph && (lo >> (32 - 8 * (p - 8))) == pl;
+}
+
+__device__ __forceinline__ int digit_of(unsigned long long hi, uint32_t lo, int p) {
+  if (p < 8) return (int)((hi >> (56 - 8 * p)) & 0xFFull);
+  return (int)((lo >> (24 - 8 * (p - 8))) & 0xFFu);
+}
+
+template <bool ONE_SEG>
+__global__ void k_hist(const int32_t* __restrict__ brow, const int32_t* __restrict__ bcol,
+                       const int32_t* __restrict__ slot, const double* __restrict__ n2, int64_t nnzb, int nb, int p,
+                       Work w) {
+  __shared__ unsigned long long sh[256];
+  if (ONE_SEG) {
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) sh[k] = 0ull;
+    __syncthreads();
+  }
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < nnzb) {
+    const int s = w.seg[t];
+    if (w.state[s] == 0) {
+      const unsigned long long hi = __double_as_longlong(n2[slot ? slot[t] : t]);
+      const uint32_t lo = (uint32_t)brow[t] * (uint32_t)nb + (uint32_t)bcol[t];
+      if (is_candidate(hi, lo, p, w.pref_hi[s], w.pref_lo[s])) {
+        const int d = digit_of(hi, lo, p);
+        if (ONE_SEG) atomicAdd(&sh[d], w.q[t]);
+        else atomicAdd(&w.hist[(int64_t)s * 256 + d], w.q[t]);
+      }
+    }
+  }
+  if (ONE_SEG) {
+    __syncthreads();
+    for (int k = threadIdx.x; k < 256; k += blockDim.x)
+      if (sh[k]) atomicAdd(&w.hist[k], sh[k]);
+  }
+}
+
+__global__ void k_select(Work w, int p) {
+  const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (s >= w.nseg || w.state[s] != 0) return;
+  unsigned long long rem = w.rem[s];
+  const unsigned long long* h = w.hist + s * 256;
+  int cut = -1;
+  for (int d = 0; d < 256; ++d) {
+    const unsigned long long v = h[d];
+    if (v <= rem) rem -= v;
+    else { cut = d; break; }
+  }
+  w.rem[s] = rem;
+  if (cut < 0) {
+    w.state[s] = 1;      // every candidate fits: drop all keys whose top 8p bits <= prefix
+    w.depth[s] = p;
+  } else if (p < 8) {
+    w.pref_hi[s] = (w.pref_hi[s] << 8) | (unsigned long long)cut;
+  } else {
+    w.pref_lo[s] = (w.pref_lo[s] << 8) | (uint32_t)cut;
+  }
+}
+
+__global__ void k_mark(const int32_t* __restrict__ brow, const int32_t* __restrict__ bcol,
+                       const int32_t* __restrict__ slot, const double* __restrict__ n2, int64_t nnzb, int nb, Work w,
+                       int32_t* keep) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnzb) return;
+  const int s = w.seg[t];
+  const unsigned long long hi = __double_as_longlong(n2[slot ? slot[t] : t]);
+  const uint32_t lo = (uint32_t)brow[t] * (uint32_t)nb + (uint32_t)bcol[t];
+  const unsigned long long ph = w.pref_hi[s];
+  const uint32_t pl = w.pref_lo[s];
+  bool drop;
+  if (w.state[s] == 1) {
+    const int dep = w.depth[s];
+    if (dep == 0) drop = true;
+    else if (dep <= 8) drop = (hi >> (64 - 8 * dep)) <= ph;
+    else {
+      const uint32_t top = lo >> (32 - 8 * (dep - 8));
+      drop = hi < ph || (hi == ph && top <= pl);
+    }
+  } else {
+    drop = hi < ph || (hi == ph && lo < pl);
+  }
+  keep[t] = drop ? 0 : 1;
+}
+
+inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+size_t trunc_work_bytes(int64_t nnzb, int nb, int64_t part_tiles) {
+  const int nsb = (int)((nb + part_tiles - 1) / part_tiles);
+  const int64_t nseg = (int64_t)nsb * nsb;
+  return align_up(nnzb * 8) + align_up(nnzb * 4) + 5 * align_up(nseg * 8) + 3 * align_up(nseg * 4) +
+         align_up(nseg * 256 * 8) + align_up((size_t)nsb * nsb * 4) + align_up((size_t)nsb * 4) + 1024;
+}
+
+// x: the tiles of X_i (slot indexes n2); n2[slot] = ||X_i tile||_F^2; keep[t] out.
+cudaError_t launch_truncate(const TileSet& x, const double* n2, int nb, double tau, int mode, int64_t part_tiles,
+                            void* work, int32_t* keep, cudaStream_t st) {
+  const int64_t nnzb = x.nnzb;
+  if (nnzb == 0) return cudaSuccess;
+  const int nsb = (int)((nb + part_tiles - 1) / part_tiles);
+  const int64_t nseg = mode == 1 ? (int64_t)nsb * nsb : 1;
+  Work w = carve(work, nnzb, nseg, nsb);
+  cudaError_t e;
+  if (mode == 1) {
+    e = cudaMemsetAsync(w.nz, 0, (size_t)nsb * nsb * 4, st);
+    if (e != cudaSuccess) return e;
+    k_nz<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, nnzb, (int)part_tiles, nsb, w.nz);
+    k_m<<<grid_for(nsb, 128), 128, 0, st>>>(w.nz, nsb, w.m);
+  }
+  k_seg_init<<<grid_for(nseg, 256), 256, 0, st>>>(w, mode, tau);
+  k_q<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, mode, (int)part_tiles, w);
+  for (int p = 0; p < 12; ++p) {
+    e = cudaMemsetAsync(w.hist, 0, (size_t)nseg * 256 * 8, st);
+    if (e != cudaSuccess) return e;
+    if (nseg == 1) k_hist<true><<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, p, w);
+    else k_hist<false><<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, p, w);
+    k_select<<<grid_for(nseg, 128), 128, 0, st>>>(w, p);
+  }
+  k_mark<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, w, keep);
+  return cudaGetLastError();
+}
+
+}  // namespace sp2

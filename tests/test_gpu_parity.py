@@ -1,0 +1,162 @@
+"""CUDA path (through the C ABI) against the CPU oracle, element by element, on
+seeded inputs that span several tiles with ragged tails.  FP64 path tolerance:
+||D_gpu - D_oracle||_F <= 1e-10; integer tile patterns bit-exact."""
+import numpy as np
+import pytest
+
+from synth import BlockSparse, dense_gapped, from_dense, make_config, to_dense
+from tests.helpers import compare, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def _case(key):
+    c = make_config(key)
+    return c
+
+
+@pytest.mark.parametrize("key", [1, "2s", "4s"])
+def test_parity_configs(key):
+    c = _case(key)
+    kw = dict(stop=c["stop"])
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    compare(g, o)
+    assert g["code"] == 0
+
+
+def test_parity_cfg1_against_projector():
+    c = _case(1)
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], 0.0, stop="idempotency")
+    import oracle.sp2_oracle as O
+    P = O.eig_projector(c["F"], c["nocc"])
+    assert np.linalg.norm(g["D"] - P) < 1e-11
+    assert abs(np.trace(g["D"]) - c["nocc"]) < 1e-10
+
+
+@pytest.mark.parametrize("mode", ["sp2", "sp2acc"])
+def test_parity_plain_sp2_and_ragged(mode):
+    # N = 100: three full tiles and a ragged tail of 4
+    d = dense_gapped(100, 37, (-2.0, -0.3), (0.4, 2.0), seed=7)
+    g = run_gpu(d["F"], d["nocc"], d["homo_ub"], d["lumo_lb"], 1e-7, mode=mode)
+    o = run_oracle(d["F"], d["nocc"], d["homo_ub"], d["lumo_lb"], 1e-7, mode=mode)
+    compare(g, o)
+
+
+def test_parity_frobinf_multiple_superblocks():
+    c = _case("3s")
+    kw = dict(trunc="frobinf", frobinf_part=1024)
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    compare(g, o)
+
+
+def test_parity_gamma_mode():
+    c = _case("2s")
+    kw = dict(gamma=1e-3)
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], 0.0, **kw)
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], 0.0, **kw)
+    compare(g, o)
+    np.testing.assert_allclose(g["stats"]["tau"], o.sched.tau, rtol=1e-14)
+
+
+@pytest.mark.parametrize("n", [2, 31, 32, 33])
+def test_tiny_and_single_tile(n):
+    nocc = max(1, n // 2)
+    d = dense_gapped(n, nocc, (-1.0, -0.5), (0.5, 1.0), seed=11 + n)
+    g = run_gpu(d["F"], d["nocc"], d["homo_ub"], d["lumo_lb"], 0.0, stop="idempotency")
+    o = run_oracle(d["F"], d["nocc"], d["homo_ub"], d["lumo_lb"], 0.0, stop="idempotency")
+    compare(g, o)
+    import oracle.sp2_oracle as O
+    assert np.linalg.norm(g["D"] - O.eig_projector(d["F"], d["nocc"])) < 1e-11
+
+
+def test_block_diagonal_input_keeps_zero_blocks_out():
+    # two decoupled molecules-worth blocks: the product pattern stays block diagonal
+    a = dense_gapped(64, 32, (-1.0, -0.5), (0.5, 1.0), seed=3)["F"]
+    b = dense_gapped(64, 32, (-1.0, -0.5), (0.5, 1.0), seed=4)["F"]
+    F = np.zeros((128, 128))
+    F[:64, :64] = a
+    F[64:, 64:] = b
+    Fb = from_dense(F)
+    assert Fb.nnzb == 6
+    g = run_gpu(Fb, 64, -0.5, 0.5, 0.0, stop="idempotency")
+    o = run_oracle(Fb, 64, -0.5, 0.5, 0.0, stop="idempotency")
+    compare(g, o)
+    assert g["brow"].shape[0] == 6
+
+
+def test_error_paths():
+    import paper_1909_12533_gb300 as sp2
+    d = dense_gapped(64, 32, (-1.0, -0.5), (0.5, 1.0), seed=5)
+    Fb = from_dense(d["F"])
+    # non-finite value
+    bad = BlockSparse(n=Fb.n, brow=Fb.brow, bcol=Fb.bcol, val=Fb.val.copy())
+    bad.val[1, 3, 4] = np.nan
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.SP2(bad, 32, -0.5, 0.5, 0.0)
+    assert e.value.code == -4
+    # unsorted pattern
+    bad = BlockSparse(n=Fb.n, brow=Fb.brow[::-1].copy(), bcol=Fb.bcol[::-1].copy(), val=Fb.val[::-1].copy())
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.SP2(bad, 32, -0.5, 0.5, 0.0)
+    assert e.value.code == -3
+    # lower-triangle tile
+    bad = BlockSparse(n=Fb.n, brow=np.array([0, 1, 1], np.int32), bcol=np.array([0, 0, 1], np.int32),
+                      val=Fb.val[:3].copy())
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.SP2(bad, 32, -0.5, 0.5, 0.0)
+    assert e.value.code == -3
+    # missing diagonal tile
+    bad = BlockSparse(n=Fb.n, brow=np.array([0, 0], np.int32), bcol=np.array([0, 1], np.int32), val=Fb.val[:2].copy())
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.SP2(bad, 32, -0.5, 0.5, 0.0)
+    assert e.value.code == -3
+    # bounds outside the Gershgorin interval
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.SP2(Fb, 32, -1e6, 0.5, 0.0)
+    assert e.value.code == -2
+    # n_max cap reached: NOT_CONVERGED, D still readable
+    ctx = sp2.SP2(Fb, 32, d["homo_ub"], d["lumo_lb"], 0.0, n_max_cap=3, stop="idempotency")
+    st = ctx.run()
+    assert ctx.code == -7 and not st["converged"] and st["n"] == 3
+    brow, bcol, val = ctx.D_host()
+    assert brow.shape[0] > 0 and np.all(np.isfinite(val))
+    ctx.close()
+
+
+def test_device_input_and_device_view():
+    import torch
+    import paper_1909_12533_gb300 as sp2
+    c = _case("2s")
+    Fb = c["F"]
+
+    class T:
+        n = Fb.n
+        brow = torch.from_numpy(Fb.brow).cuda()
+        bcol = torch.from_numpy(Fb.bcol).cuda()
+        val = torch.from_numpy(Fb.val).cuda()
+
+    ctx = sp2.SP2(T, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"])
+    st = ctx.run()
+    brow, bcol, val = ctx.D_device()
+    hb, hc, hv = ctx.D_host()
+    assert np.array_equal(brow.cpu().numpy(), hb) and np.array_equal(bcol.cpu().numpy(), hc)
+    assert np.array_equal(val.cpu().numpy(), hv)
+    g = run_gpu(Fb, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"])
+    assert np.array_equal(g["val"], hv)  # host and device inputs give identical results
+    assert st["n"] == g["stats"]["n"]
+    ctx.close()
+
+
+def test_run_twice_is_deterministic():
+    import paper_1909_12533_gb300 as sp2
+    c = _case("4s")
+    ctx = sp2.SP2(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"])
+    s1 = ctx.run()
+    d1 = ctx.D_host()
+    s2 = ctx.run()
+    d2 = ctx.D_host()
+    ctx.close()
+    assert s1["e"] == s2["e"] and s1["t"] == s2["t"]
+    assert all(np.array_equal(a, b) for a, b in zip(d1, d2))
