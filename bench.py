@@ -1,0 +1,283 @@
+#!/usr/bin/env python
+"""SP2 time-to-D and effective TFLOP/s on one GB300 (whole SP2ACC expansion per step).
+
+Workload (default): the water-like Fock matrix with 1000 molecules, N = 24000,
+tile b = 32, tau = 1e-6, Frobenius truncation, parameterless stop.  It is a
+seeded synthetic stand-in for the paper's HF/3-21G water clusters.
+A step is one full pass of the method: sp2_create from the device-resident F
+(Gershgorin bounds, schedule, X_0), then sp2_run (every iteration's symbolic
+square, tile products with the fused epilogue, reductions, stop test,
+truncation and compaction, then Step 3), ending with D on the device.
+
+value = algorithmic FLOP/s of the whole job (2 * 32^3 per (I <= J, K) tile
+triplet, summed over every square executed) / device time of the timed steps.
+With --gpus N > 1 each rank runs an independent replica (the path runs on one
+GPU; value sums all ranks' flops over the slowest rank's time).
+
+--impl reference times the CPU oracle (plain numpy FP64) on a bounded sample of
+the same recipe (101 molecules, N = 2424) on this host's cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+from pathlib import Path
+
+ROOT = Path(__file__).resolve().parent
+sys.path.insert(0, str(ROOT))
+
+METRIC = "SP2 time-to-D & eff. TFLOP/s, mixed vs FP64 GPU path at ||D-Dref||_F<=1e-6"
+WORKLOADS = {
+    "water24k": dict(key=2, desc="water-like, 1000 molecules x 24 basis functions, N=24000, b=32, tau=1e-6, "
+                               "Frobenius truncation, parameterless stop"),
+    "water2k": dict(key="2s", desc="water-like, 101 molecules, N=2424, b=32, tau=1e-6"),
+    "helix128k": dict(key=4, desc="helix-like chain, 2000 residues x 64, N=128000, tau=1e-6"),
+    "dense512": dict(key=1, desc="dense N=512, tau=0, idempotency stop 1e-12"),
+}
+CPU_SAMPLE_KEY = "2s"
+PEAK_FP64_TFLOPS = 1.25   # GB300 FP64 nominal (no FP64 tensor path on this chip)
+
+
+def measured_peaks() -> dict:
+    p = ROOT / "MEASURED_PEAKS.json"
+    if p.exists():
+        return json.loads(p.read_text())
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0, "fallback": True}
+
+
+class ClockSampler:
+    """Samples SM clocks and throttle reasons with nvidia-smi while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.rows = []
+        self.proc = None
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.idx), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) >= 9:
+                self.rows.append(parts)
+
+    def stop(self) -> dict:
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm = [float(r[1]) for r in self.rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in self.rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in self.rows for k in range(4) if r[5 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(self.rows)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def cpu_oracle_sample() -> dict:
+    """The CPU oracle as it stands on a bounded sample of the same recipe."""
+    import oracle.sp2_oracle as O
+    from synth import make_config, to_dense
+    c = make_config(CPU_SAMPLE_KEY)
+    F = to_dense(c["F"])
+    pattern = set(zip(c["F"].brow.tolist(), c["F"].bcol.tolist()))
+    t0 = time.perf_counter()
+    r = O.sp2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], tau=c["tau"], input_pattern=pattern)
+    dt = time.perf_counter() - t0
+    flops = 2.0 * 32 ** 3 * r.tile_triplets
+    return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "seconds": dt, "flops": flops, "iterations": r.n,
+            "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
+            "sample": f"full SP2ACC run of the oracle (dense numpy FP64) on the same water-like recipe at "
+                      f"101 molecules (N={F.shape[0]}) instead of 1000"}
+
+
+def run_reference(args):
+    rank, world, _ = dist_env()
+    if rank != 0:
+        return 0
+    for _ in range(args.warmup):
+        cpu_oracle_sample()
+    samples = [cpu_oracle_sample() for _ in range(args.steps)]
+    tot_flops = sum(s["flops"] for s in samples)
+    tot_s = sum(s["seconds"] for s in samples)
+    v = tot_flops / tot_s / 1e12
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": samples[0]["sample"], "l2": "n/a (CPU)"},
+            "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": samples[0]["cores"], "kind": "oracle",
+                             "sample": samples[0]["sample"]},
+            "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main(argv=None) -> int:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="water24k", choices=sorted(WORKLOADS))
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "split16"])
+    ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import paper_1909_12533_gb300 as sp2
+    from synth import make_config
+
+    rank, world, local = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    sp2.load()  # fails loudly if the library is missing
+
+    wl = WORKLOADS[args.workload]
+    c = make_config(wl["key"])
+    from synth import from_dense
+    Fh = c["F"] if not isinstance(c["F"], np.ndarray) else from_dense(c["F"])
+
+    class Dev:
+        n = Fh.n
+        brow = torch.from_numpy(Fh.brow).cuda()
+        bcol = torch.from_numpy(Fh.bcol).cuda()
+        val = torch.from_numpy(Fh.val).cuda()
+
+    prm = dict(stop=c["stop"], precision=args.precision, slices=args.slices)
+    stream = torch.cuda.current_stream()
+
+    def step(F):
+        ctx = sp2.SP2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **prm)
+        st = ctx.run()
+        ctx.close()
+        return st
+
+    for _ in range(args.warmup):
+        step(Dev)
+    torch.cuda.synchronize()
+    if world > 1:
+        torch.distributed.barrier()
+    clocks = ClockSampler(local)
+    clocks.start()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    stats = [step(Dev) for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    if world > 1:
+        torch.distributed.barrier()
+    ms = e0.elapsed_time(e1)
+    flops = sum(s["alg_flops"] for s in stats)
+    sq_ms = sum(s["square_ms"] for s in stats)
+    squares = sum(s["squares"] for s in stats)
+    launches = sum(s["kernel_launches"] for s in stats)
+    t = torch.tensor([ms, flops], dtype=torch.float64, device="cuda")
+    if world > 1:
+        mx = t.clone()
+        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
+        sm = t.clone()
+        torch.distributed.all_reduce(sm[1:], op=torch.distributed.ReduceOp.SUM)
+        ms_max, flops_all = float(mx[0]), float(sm[1])
+    else:
+        ms_max, flops_all = ms, flops
+    value = flops_all / (ms_max / 1e3) / 1e12
+
+    # end to end through the public API with host buffers (H2D of F and D2H of D timed)
+    e2e = None
+    if not args.no_e2e:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        ctx = sp2.SP2(Fh, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **prm)
+        st = ctx.run()
+        brow, bcol, val = ctx.D_host()
+        ctx.close()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h2d = Fh.val.nbytes + Fh.brow.nbytes + Fh.bcol.nbytes
+        d2h = val.nbytes + brow.nbytes + bcol.nbytes
+        e2e = {"value": st["alg_flops"] / dt / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "seconds": dt}
+
+    if rank != 0:
+        return 0
+    peaks = measured_peaks()
+    per_launch_flops = flops / max(squares, 1)
+    per_launch_ms = sq_ms / max(squares, 1)
+    achieved = per_launch_flops / (per_launch_ms / 1e3) / 1e12 if per_launch_ms > 0 else 0.0
+    if args.precision == "fp64":
+        roof = {"bound": "alu", "achieved": achieved, "peak": PEAK_FP64_TFLOPS, "unit": "TFLOP/s",
+                "frac": achieved / PEAK_FP64_TFLOPS, "traffic": None, "kernel": "k_square_f64",
+                "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 tensor path); measured DFMA 1.19"}
+    else:
+        pk = peaks["bf16_tflops_sustained"]
+        roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
+                "traffic": None, "kernel": "k_square_split16",
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (FP16 runs at the BF16 rate)"}
+    s0 = stats[-1]
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f16-split+f64",
+        "data": "synthetic",
+        "config": {"workload": wl["desc"], "precision": args.precision,
+                   "slices": args.slices if args.precision == "split16" else None,
+                   "l2": "inputs larger than L2 (F alone is %.0f MB)" % (Fh.val.nbytes / 1e6),
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "time_to_D_ms": ms_max / args.steps, "iterations": s0["n"], "squares": s0["squares"],
+        "alg_flops_per_step": s0["alg_flops"], "nnzb_final": s0["nnzb_final"],
+        "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
+    }
+    if not args.no_cpu_baseline and world == 1:
+        cb = cpu_oracle_sample()
+        line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
+    print(json.dumps(line), flush=True)
+    if world > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -127,6 +127,7 @@ typedef struct {
   double t[SP2_MAX_ITER];         /* t_j                                               */
   int64_t nnzb_hist[SP2_MAX_ITER]; /* stored tiles of X~_j                             */
   int32_t prec_hist[SP2_MAX_ITER]; /* precision of the square that produced e_j         */
+  int64_t kernel_launches;        /* kernels this library launched during sp2_run      */
 } sp2_stats;
 
 typedef struct sp2_ctx sp2_ctx;

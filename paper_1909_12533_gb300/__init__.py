@@ -56,7 +56,7 @@ class sp2_stats(ctypes.Structure):
                 ("tile_triplets", c_int64), ("alg_flops", c_double), ("run_ms", c_double), ("square_ms", c_double),
                 ("p", c_int32 * MAX_ITER), ("alpha", c_double * MAX_ITER), ("tau", c_double * MAX_ITER),
                 ("e", c_double * MAX_ITER), ("t", c_double * MAX_ITER), ("nnzb_hist", c_int64 * MAX_ITER),
-                ("prec_hist", c_int32 * MAX_ITER)]
+                ("prec_hist", c_int32 * MAX_ITER), ("kernel_launches", c_int64)]
 
 
 # Entry points declared in include/sp2.h: (name, restype, argtypes)

@@ -43,20 +43,20 @@ cudaError_t launch_compact(const TileSet& in, const int32_t* keep, int nb, TileS
   cudaError_t e = launch_scan_i32(keep, scan_buf, in.nnzb, count_dev, scan_tmp, st);
   if (e != cudaSuccess) return e;
   if (in.nnzb > 0)
-    k_scatter<<<grid_for(in.nnzb, 256), 256, 0, st>>>(keep, scan_buf, in.nnzb, in.brow, in.bcol, in.slot, out.brow,
-                                                       out.bcol, out.slot);
+    { ++g_launches; k_scatter<<<grid_for(in.nnzb, 256), 256, 0, st>>>(keep, scan_buf, in.nnzb, in.brow, in.bcol, in.slot, out.brow,
+                                                       out.bcol, out.slot); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_gather_tiles(const TileSet& s, const double* pool, double* dst, cudaStream_t st) {
   if (s.nnzb == 0) return cudaSuccess;
-  k_gather<<<(unsigned)s.nnzb, 256, 0, st>>>(s.slot, pool, dst);
+  { ++g_launches; k_gather<<<(unsigned)s.nnzb, 256, 0, st>>>(s.slot, pool, dst); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_copy_index(const TileSet& s, int32_t* brow, int32_t* bcol, cudaStream_t st) {
   if (s.nnzb == 0) return cudaSuccess;
-  k_copy2<<<grid_for(s.nnzb, 256), 256, 0, st>>>(s.brow, s.bcol, s.nnzb, brow, bcol);
+  { ++g_launches; k_copy2<<<grid_for(s.nnzb, 256), 256, 0, st>>>(s.brow, s.bcol, s.nnzb, brow, bcol); }
   return cudaGetLastError();
 }
 

@@ -94,19 +94,19 @@ __global__ void __launch_bounds__(256) k_x0(const int32_t* __restrict__ brow, co
 cudaError_t launch_gershgorin(const FullPattern& fp, const double* pool, int nb, int64_t n, double* rowlo,
                               double* rowhi, cudaStream_t st) {
   const int64_t thr = (int64_t)nb * 32;
-  k_gershgorin<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(fp.rowptr, fp.col, fp.ref, pool, nb, n, rowlo, rowhi);
+  { ++g_launches; k_gershgorin<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(fp.rowptr, fp.col, fp.ref, pool, nb, n, rowlo, rowhi); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_minmax(const double* lo, const double* hi, int64_t n, double* out2, cudaStream_t st) {
-  k_minmax<<<1, 1024, 0, st>>>(lo, hi, n, out2);
+  { ++g_launches; k_minmax<<<1, 1024, 0, st>>>(lo, hi, n, out2); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_x0(const TileSet& f, const double* fpool, double* xpool, int64_t n, double lmax, double w,
                       double* n2, cudaStream_t st) {
   if (f.nnzb == 0) return cudaSuccess;
-  k_x0<<<(unsigned)f.nnzb, 256, 0, st>>>(f.brow, f.bcol, f.slot, fpool, xpool, n, lmax, w, n2);
+  { ++g_launches; k_x0<<<(unsigned)f.nnzb, 256, 0, st>>>(f.brow, f.bcol, f.slot, fpool, xpool, n, lmax, w, n2); }
   return cudaGetLastError();
 }
 

@@ -236,45 +236,45 @@ cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t n, int
   }
   const int64_t nch = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
   int32_t* cs = static_cast<int32_t*>(tmp);
-  k_scan_chunks<<<(unsigned)nch, SCAN_T, 0, st>>>(in, n, cs);
-  k_scan_partials<<<1, SCAN_T, 0, st>>>(cs, nch, total_dev);
-  k_scan_apply<<<(unsigned)nch, SCAN_T, 0, st>>>(in, n, cs, out_excl);
+  { ++g_launches; k_scan_chunks<<<(unsigned)nch, SCAN_T, 0, st>>>(in, n, cs); }
+  { ++g_launches; k_scan_partials<<<1, SCAN_T, 0, st>>>(cs, nch, total_dev); }
+  { ++g_launches; k_scan_apply<<<(unsigned)nch, SCAN_T, 0, st>>>(in, n, cs, out_excl); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_bitmap(const TileSet& s, int nb, FullPattern& fp, cudaStream_t st) {
   cudaError_t e = cudaMemsetAsync(fp.bits, 0, (size_t)nb * fp.words * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  if (s.nnzb > 0) k_bitmap<<<grid_for(s.nnzb, 256), 256, 0, st>>>(s.brow, s.bcol, s.nnzb, fp.bits, fp.words);
+  if (s.nnzb > 0) { ++g_launches; k_bitmap<<<grid_for(s.nnzb, 256), 256, 0, st>>>(s.brow, s.bcol, s.nnzb, fp.bits, fp.words); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_row_popc(const uint32_t* bits, int nb, int words, int32_t* counts, cudaStream_t st) {
-  k_row_popc<<<grid_for((int64_t)nb * 32, 256), 256, 0, st>>>(bits, nb, words, counts);
+  { ++g_launches; k_row_popc<<<grid_for((int64_t)nb * 32, 256), 256, 0, st>>>(bits, nb, words, counts); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_full(const TileSet& s, int nb, FullPattern& fp, cudaStream_t st) {
-  k_fill_full<<<grid_for((int64_t)nb * 32, 256), 256, 0, st>>>(fp.bits, nb, fp.words, fp.rowptr, s.rowptr, s.bcol,
-                                                                s.slot, fp.col, fp.ref);
+  { ++g_launches; k_fill_full<<<grid_for((int64_t)nb * 32, 256), 256, 0, st>>>(fp.bits, nb, fp.words, fp.rowptr, s.rowptr, s.bcol,
+                                                                s.slot, fp.col, fp.ref); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_product_bits(const FullPattern& a, const FullPattern& b, int nb, uint32_t* out_bits,
                                 cudaStream_t st) {
   const int t = a.words >= 128 ? 256 : (a.words >= 32 ? 128 : 32);
-  k_product_bits<<<nb, t, 0, st>>>(a.rowptr, a.col, b.bits, nb, a.words, out_bits);
+  { ++g_launches; k_product_bits<<<nb, t, 0, st>>>(a.rowptr, a.col, b.bits, nb, a.words, out_bits); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_fill_upper_from_bits(const uint32_t* bits, int nb, int words, const int32_t* rowptr,
                                         int32_t* brow, int32_t* bcol, int32_t* slot, cudaStream_t st) {
-  k_fill_upper<<<grid_for((int64_t)nb * 32, 256), 256, 0, st>>>(bits, nb, words, rowptr, brow, bcol, slot);
+  { ++g_launches; k_fill_upper<<<grid_for((int64_t)nb * 32, 256), 256, 0, st>>>(bits, nb, words, rowptr, brow, bcol, slot); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_rowptr_from_brow(const int32_t* brow, int64_t nnzb, int nb, int32_t* rowptr, cudaStream_t st) {
-  k_rowptr<<<grid_for(nb + 1, 256), 256, 0, st>>>(brow, nnzb, nb, rowptr);
+  { ++g_launches; k_rowptr<<<grid_for(nb + 1, 256), 256, 0, st>>>(brow, nnzb, nb, rowptr); }
   return cudaGetLastError();
 }
 
@@ -285,11 +285,11 @@ cudaError_t launch_check_pattern(const int32_t* brow, const int32_t* bcol, int64
   cudaError_t e = cudaMemsetAsync(flag, 0, 2 * sizeof(int32_t), st);
   if (e != cudaSuccess) return e;
   if (nnzb > 0) {
-    k_check_pattern<<<grid_for(nnzb, 256), 256, 0, st>>>(brow, bcol, nnzb, nb, flag, flag + 1);
+    { ++g_launches; k_check_pattern<<<grid_for(nnzb, 256), 256, 0, st>>>(brow, bcol, nnzb, nb, flag, flag + 1); }
     const int64_t cnt = nnzb * TE;
     unsigned g = grid_for(cnt, 256);
     if (g > 152u * 32u) g = 152u * 32u;
-    k_check_finite<<<g, 256, 0, st>>>(val, cnt, flag);
+    { ++g_launches; k_check_finite<<<g, 256, 0, st>>>(val, cnt, flag); }
   }
   return cudaGetLastError();
 }

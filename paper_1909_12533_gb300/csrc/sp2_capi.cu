@@ -16,6 +16,10 @@
 
 using namespace sp2;
 
+namespace sp2 {
+long long g_launches = 0;
+}
+
 namespace {
 
 constexpr double C_STOP = 6.8872;  // Algorithm 2
@@ -549,6 +553,7 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       S.nnzb_hist[i] = -1;
       S.prec_hist[i] = -1;
     }
+    const long long launches0 = g_launches;
     c->ck(cudaEventRecord(c->ev0, c->st), "event");
     // Algorithm 1: X_0 on F's pattern, then X~_0 = trunc(X_0, tau_0)
     const int64_t nF = c->F.nnzb;
@@ -643,6 +648,7 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
     float ms = 0.f;
     c->ck(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "elapsed");
     S.run_ms = ms;
+    S.kernel_launches = g_launches - launches0;
     S.n = n_out;
     S.converged = converged ? 1 : 0;
     S.nnzb_final = c->d_nnzb;

@@ -37,6 +37,9 @@ struct FullPattern {
 
 constexpr uint32_t REF_T = 0x80000000u;
 
+// Host-side count of the kernels this library has launched (reported per run).
+extern long long g_launches;
+
 // Per-output-tile partial sums written by the fused epilogue.
 struct Partials {
   double* e2 = nullptr;       // w * ||X~_IJ - S_IJ||_F^2  (w = 2 off the diagonal)

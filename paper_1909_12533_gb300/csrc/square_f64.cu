@@ -211,13 +211,13 @@ cudaError_t launch_square_f64(const SquareArgs& a, cudaStream_t st) {
   d.c0 = a.c0; d.c1 = a.c1; d.c2 = a.c2;
   d.n = a.n; d.words = a.A->words;
   d.part = a.part;
-  if (a.sym_sum) k_square_f64<true><<<(unsigned)a.out->nnzb, 256, 0, st>>>(d);
-  else k_square_f64<false><<<(unsigned)a.out->nnzb, 256, 0, st>>>(d);
+  if (a.sym_sum) { ++g_launches; k_square_f64<true><<<(unsigned)a.out->nnzb, 256, 0, st>>>(d); }
+  else { ++g_launches; k_square_f64<false><<<(unsigned)a.out->nnzb, 256, 0, st>>>(d); }
   return cudaGetLastError();
 }
 
 cudaError_t launch_reduce_step(const Partials& p, int64_t ntiles, StepScalars* out, cudaStream_t st) {
-  k_reduce_step<<<1, 1024, 0, st>>>(p, ntiles, out);
+  { ++g_launches; k_reduce_step<<<1, 1024, 0, st>>>(p, ntiles, out); }
   return cudaGetLastError();
 }
 

@@ -239,19 +239,19 @@ cudaError_t launch_truncate(const TileSet& x, const double* n2, int nb, double t
   if (mode == 1) {
     e = cudaMemsetAsync(w.nz, 0, (size_t)nsb * nsb * 4, st);
     if (e != cudaSuccess) return e;
-    k_nz<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, nnzb, (int)part_tiles, nsb, w.nz);
-    k_m<<<grid_for(nsb, 128), 128, 0, st>>>(w.nz, nsb, w.m);
+    { ++g_launches; k_nz<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, nnzb, (int)part_tiles, nsb, w.nz); }
+    { ++g_launches; k_m<<<grid_for(nsb, 128), 128, 0, st>>>(w.nz, nsb, w.m); }
   }
-  k_seg_init<<<grid_for(nseg, 256), 256, 0, st>>>(w, mode, tau);
-  k_q<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, mode, (int)part_tiles, w);
+  { ++g_launches; k_seg_init<<<grid_for(nseg, 256), 256, 0, st>>>(w, mode, tau); }
+  { ++g_launches; k_q<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, mode, (int)part_tiles, w); }
   for (int p = 0; p < 12; ++p) {
     e = cudaMemsetAsync(w.hist, 0, (size_t)nseg * 256 * 8, st);
     if (e != cudaSuccess) return e;
-    if (nseg == 1) k_hist<true><<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, p, w);
-    else k_hist<false><<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, p, w);
-    k_select<<<grid_for(nseg, 128), 128, 0, st>>>(w, p);
+    if (nseg == 1) { ++g_launches; k_hist<true><<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, p, w); }
+    else { ++g_launches; k_hist<false><<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, p, w); }
+    { ++g_launches; k_select<<<grid_for(nseg, 128), 128, 0, st>>>(w, p); }
   }
-  k_mark<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, w, keep);
+  { ++g_launches; k_mark<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, w, keep); }
   return cudaGetLastError();
 }
 
