@@ -128,6 +128,7 @@ typedef struct {
   int64_t nnzb_hist[SP2_MAX_ITER]; /* stored tiles of X~_j                             */
   int32_t prec_hist[SP2_MAX_ITER]; /* precision of the square that produced e_j         */
   int64_t kernel_launches;        /* kernels this library launched during sp2_run      */
+  double backward_ms;             /* device time of the last sp2_backward              */
 } sp2_stats;
 
 typedef struct sp2_ctx sp2_ctx;
@@ -169,6 +170,20 @@ int sp2_copy_D(sp2_ctx* ctx, int32_t* brow, int32_t* bcol, double* val, int64_t 
  * sp2_get_D).  The iterates are recomputed from checkpoints every ckpt_every
  * steps with the recorded truncation masks.  Requires record_masks = 1. */
 int sp2_backward(sp2_ctx* ctx, const sp2_bsr* W, sp2_bsr* dF_view);
+
+/* Truncation step of Algorithm 2 as a standalone call (Section 2, Eq. (8):
+ * X~ = X + E with ||E|| <= tau; Frob-Inf norm of Section 3, Eq. (13)).  X: the
+ * stored upper tiles of a symmetric matrix (host or device per X->on_device;
+ * X is not modified).  Tiles are ranked by (||X_IJ||_F^2, I * nb + J) and the
+ * longest ascending prefix whose squared norms (weight 2 for mirrored tiles)
+ * fit into tau^2 is dropped -- per Frob-Inf super-block with the budget
+ * tau / max(m_R, m_C) in FROBINF mode (frobinf_part rows, multiple of 32).
+ * Budget sums are exact integers in units of budget * 2^-36 (shares rounded
+ * up).  keep[nnzb] (same residency as X) receives 1 = kept, 0 = dropped.
+ * Allocates its scratch with cudaMallocAsync on cuda_stream and synchronises
+ * that stream before returning.  Errors: INVALID_ARG, OOM, CUDA. */
+int sp2_truncate(const sp2_bsr* X, double tau, int32_t mode, int64_t frobinf_part, int32_t* keep,
+                 void* cuda_stream);
 
 int sp2_get_stats(const sp2_ctx* ctx, sp2_stats* stats);
 void sp2_destroy(sp2_ctx* ctx);

@@ -56,7 +56,8 @@ class sp2_stats(ctypes.Structure):
                 ("tile_triplets", c_int64), ("alg_flops", c_double), ("run_ms", c_double), ("square_ms", c_double),
                 ("p", c_int32 * MAX_ITER), ("alpha", c_double * MAX_ITER), ("tau", c_double * MAX_ITER),
                 ("e", c_double * MAX_ITER), ("t", c_double * MAX_ITER), ("nnzb_hist", c_int64 * MAX_ITER),
-                ("prec_hist", c_int32 * MAX_ITER), ("kernel_launches", c_int64)]
+                ("prec_hist", c_int32 * MAX_ITER), ("kernel_launches", c_int64),
+                ("backward_ms", c_double)]
 
 
 # Entry points declared in include/sp2.h: (name, restype, argtypes)
@@ -68,6 +69,7 @@ _SIGS = [
     ("sp2_get_D", c_int32, [c_void_p, POINTER(sp2_bsr)]),
     ("sp2_copy_D", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, POINTER(c_int64)]),
     ("sp2_backward", c_int32, [c_void_p, POINTER(sp2_bsr), POINTER(sp2_bsr)]),
+    ("sp2_truncate", c_int32, [POINTER(sp2_bsr), c_double, c_int32, c_int64, c_void_p, c_void_p]),
     ("sp2_get_stats", c_int32, [c_void_p, POINTER(sp2_stats)]),
     ("sp2_destroy", None, [c_void_p]),
     ("sp2_strerror", ctypes.c_char_p, [c_int32]),
@@ -215,6 +217,25 @@ def sp2_backward(ctx, W) -> sp2_bsr:
     return out
 
 
+def sp2_truncate(X, tau: float, mode="frobenius", frobinf_part: int = 4096, stream=None):
+    """Keep flags (1 = kept) of X's tiles after the truncation of Eq. (8).
+    Host inputs give a numpy array, device inputs a torch CUDA tensor."""
+    bsr, keep_alive = make_bsr(X.n, X.brow, X.bcol, X.val)
+    m = TRUNCS[mode] if isinstance(mode, str) else int(mode)
+    if bsr.on_device:
+        import torch
+        keep = torch.empty(bsr.nnzb, dtype=torch.int32, device="cuda")
+        kp = keep.data_ptr()
+    else:
+        keep = np.empty(bsr.nnzb, np.int32)
+        kp = keep.ctypes.data
+    rc = load().sp2_truncate(byref(bsr), float(tau), m, int(frobinf_part), c_void_p(kp), _stream_handle(stream))
+    del keep_alive
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_truncate")
+    return keep
+
+
 def sp2_get_stats(ctx) -> sp2_stats:
     st = sp2_stats()
     rc = load().sp2_get_stats(ctx, byref(st))
@@ -328,3 +349,58 @@ def header_functions() -> list[str]:
     import re
     h = (Path(__file__).resolve().parent.parent / "include" / "sp2.h").read_text()
     return sorted(set(re.findall(r"\b(sp2_[A-Za-z0-9_]+)\s*\(", h)))
+
+
+# ------------------------------------------------------------------ autograd
+def _autograd_function():
+    import torch
+
+    class _Tiles:
+        def __init__(self, n, brow, bcol, val):
+            self.n, self.brow, self.bcol, self.val = n, brow, bcol, val
+
+    class SP2Function(torch.autograd.Function):
+        """D = SP2ACC(F) on the tile pattern of F (stored upper tiles, CUDA tensors).
+
+        forward(F_val, F_brow, F_bcol, n, nocc, homo_ub, lumo_lb, tau, params)
+        returns (D_val, D_brow, D_bcol); only D_val carries a gradient.
+        backward: for L with dL/dD_val = gD, W = gD on D's pattern with
+        off-diagonal tiles halved (each stands for two blocks of the symmetric
+        D), so L = trace(D W); sp2_backward gives dF_ij = dL/dF_ij, and a stored
+        off-diagonal F tile (F_IJ and F_JI) receives 2 dF_IJ."""
+
+        @staticmethod
+        def forward(ctx, F_val, F_brow, F_bcol, n, nocc, homo_ub, lumo_lb, tau, params=None):
+            F = _Tiles(int(n), F_brow, F_bcol, F_val.detach())
+            obj = SP2(F, nocc, homo_ub, lumo_lb, tau, **(params or {}))
+            obj.run()
+            if obj.code not in (SP2_OK, NOT_CONVERGED):
+                raise SP2Error(obj.code, "sp2_run")
+            d_brow, d_bcol, d_val = obj.D_device()
+            ctx.obj = obj
+            ctx.n = int(n)
+            ctx.f_off = (F_brow != F_bcol)
+            ctx.save_for_backward(d_brow, d_bcol)
+            ctx.mark_non_differentiable(d_brow, d_bcol)
+            return d_val, d_brow, d_bcol
+
+        @staticmethod
+        def backward(ctx, g_val, _g_brow, _g_bcol):
+            d_brow, d_bcol = ctx.saved_tensors
+            w = g_val.detach().to(torch.float64).clone()
+            off = d_brow != d_bcol
+            w[off] *= 0.5
+            W = _Tiles(ctx.n, d_brow, d_bcol, w.contiguous())
+            _, _, dF = ctx.obj.backward(W)
+            dF = dF.clone()
+            dF[ctx.f_off] *= 2.0
+            ctx.obj.close()
+            return dF, None, None, None, None, None, None, None, None
+
+    return SP2Function
+
+
+def __getattr__(name):
+    if name == "SP2Function":
+        return _autograd_function()
+    raise AttributeError(name)

@@ -34,9 +34,60 @@ __global__ void k_copy2(const int32_t* __restrict__ a, const int32_t* __restrict
   ob[t] = b[t];
 }
 
+__device__ __forceinline__ int64_t find_tile(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ bcol,
+                                             int I, int J) {
+  int64_t lo = rowptr[I], hi = rowptr[I + 1];
+  while (lo < hi) {
+    const int64_t mid = (lo + hi) >> 1;
+    if (bcol[mid] < J) lo = mid + 1; else hi = mid;
+  }
+  return (lo < rowptr[I + 1] && bcol[lo] == J) ? lo : -1;
+}
+
+// dst tile t := scale * src tile (I, J) (0 when src has no such tile); with
+// sym_diag the diagonal tiles are symmetrised, (W + W^T) / 2.
+__global__ void __launch_bounds__(256) k_place(const int32_t* __restrict__ srowptr, const int32_t* __restrict__ sbcol,
+                                               const int32_t* __restrict__ sslot, const double* __restrict__ spool,
+                                               const int32_t* __restrict__ dbrow, const int32_t* __restrict__ dbcol,
+                                               const int32_t* __restrict__ dslot, double* dpool, double scale,
+                                               int sym_diag) {
+  const int64_t t = blockIdx.x;
+  const int I = dbrow[t], J = dbcol[t];
+  const int64_t k = find_tile(srowptr, sbcol, I, J);
+  double* d = dpool + (int64_t)(dslot ? dslot[t] : t) * TE;
+  if (k < 0) {
+    for (int q = threadIdx.x; q < TE; q += 256) d[q] = 0.0;
+    return;
+  }
+  const double* s = spool + (int64_t)(sslot ? sslot[k] : k) * TE;
+  for (int q = threadIdx.x; q < TE; q += 256) {
+    double v = s[q];
+    if (sym_diag && I == J) v = 0.5 * (v + s[(q & 31) * TB + (q >> 5)]);
+    d[q] = scale * v;
+  }
+}
+
+__global__ void k_iota(int32_t* p, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) p[i] = (int32_t)i;
+}
+
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_place(const TileSet& src, const double* spool, const TileSet& dst, double* dpool, double scale,
+                         int sym_diag, cudaStream_t st) {
+  if (dst.nnzb == 0) return cudaSuccess;
+  { ++g_launches; k_place<<<(unsigned)dst.nnzb, 256, 0, st>>>(src.rowptr, src.bcol, src.slot, spool, dst.brow, dst.bcol, dst.slot, dpool, scale, sym_diag); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_iota(int32_t* p, int64_t n, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  { ++g_launches; k_iota<<<grid_for(n, 256), 256, 0, st>>>(p, n); }
+  return cudaGetLastError();
+}
 
 cudaError_t launch_compact(const TileSet& in, const int32_t* keep, int nb, TileSet& out, int32_t* count_dev,
                            void* scan_tmp, int32_t* scan_buf, cudaStream_t st) {

@@ -225,6 +225,14 @@ struct Fail {
   int code;
 };
 
+// Per-iteration record for the adjoint: the kept tiles of X~_j and, every
+// ckpt_every steps, their FP64 values (contiguous, index order).
+struct Rec {
+  Buf brow, bcol, rowptr, val;
+  int64_t nnzb = 0;
+  bool has_val = false;
+};
+
 }  // namespace
 
 struct sp2_ctx {
@@ -247,6 +255,13 @@ struct sp2_ctx {
   Buf fp_bits, fp_rowptr, fp_col, fp_ref, counts;
   Buf p_e2, p_trS, p_trX, p_n2, p_kt, keep, scanbuf, scantmp, twork, rowlo, rowhi;
   Buf dsc, dcnt, d2;
+  Buf slices, zero16, sbits, sflag, spos, slist, errflag;
+  // adjoint
+  std::vector<Rec> recs;
+  std::vector<Buf> seg;
+  Buf ident, fpB_bits, fpB_rowptr, fpB_col, fpB_ref, gpool[2], w_brow, w_bcol, w_rowptr, w_pool, dF;
+  FullPattern fpB;
+  double backward_ms = 0.0;
   StepScalars* h_sc = nullptr;
   int32_t* h_cnt = nullptr;
   double* h_d2 = nullptr;
@@ -262,7 +277,9 @@ struct sp2_ctx {
     Buf* all[] = {&f_brow, &f_bcol, &f_slot, &f_rowptr, &f_pool, &x_brow, &x_bcol, &x_slot, &x_rowptr,
                   &o_brow, &o_bcol, &o_slot, &o_rowptr, &o_bits, &pool[0], &pool[1], &fp_bits, &fp_rowptr,
                   &fp_col, &fp_ref, &counts, &p_e2, &p_trS, &p_trX, &p_n2, &p_kt, &keep, &scanbuf, &scantmp,
-                  &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val};
+                  &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &slices, &zero16,
+                  &sbits, &sflag, &spos, &slist, &errflag, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
+                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF};
     for (Buf* b : all) bufs.push_back(b);
   }
 
@@ -369,6 +386,106 @@ void truncate_into_X(sp2_ctx* c, const TileSet& in, const double* n2, double tau
         "compact");
   c->X.nnzb = read_count(c, c->dcnt.as<int32_t>());
   c->ck(launch_rowptr_from_brow(c->X.brow, c->X.nnzb, c->nb, c->X.rowptr, c->st), "rowptr");
+}
+
+void free_recs(sp2_ctx* c) {
+  for (Rec& r : c->recs)
+    for (Buf* b : {&r.brow, &r.bcol, &r.rowptr, &r.val}) {
+      c->al.put(b->p);
+      b->p = nullptr;
+      b->cap = 0;
+    }
+  c->recs.clear();
+  for (Buf& b : c->seg) c->al.put(b.p);
+  c->seg.clear();
+}
+
+void ensure_ident(sp2_ctx* c, int64_t n) {
+  if (c->ident.p && c->ident.cap >= (size_t)n * 4) return;
+  c->ensure(c->ident, (size_t)std::max<int64_t>(n, 1) * 4);
+  c->ck(launch_iota(c->ident.as<int32_t>(), (int64_t)(c->ident.cap / 4), c->st), "iota");
+}
+
+void record(sp2_ctx* c, int j) {
+  if (!c->prm.record_masks) return;
+  if ((int)c->recs.size() <= j) c->recs.resize(j + 1);
+  Rec& r = c->recs[j];
+  r.nnzb = c->X.nnzb;
+  c->ensure(r.brow, (size_t)std::max<int64_t>(r.nnzb, 1) * 4);
+  c->ensure(r.bcol, (size_t)std::max<int64_t>(r.nnzb, 1) * 4);
+  c->ensure(r.rowptr, (size_t)(c->nb + 1) * 4);
+  c->ck(launch_copy_index(c->X, r.brow.as<int32_t>(), r.bcol.as<int32_t>(), c->st), "record index");
+  c->ck(launch_rowptr_from_brow(r.brow.as<int32_t>(), r.nnzb, c->nb, r.rowptr.as<int32_t>(), c->st), "rowptr");
+  r.has_val = (j % c->prm.ckpt_every) == 0;
+  if (r.has_val) {
+    c->ensure(r.val, (size_t)std::max<int64_t>(r.nnzb, 1) * TE * 8);
+    c->ck(launch_gather_tiles(c->X, c->pool[c->cur].as<double>(), r.val.as<double>(), c->st), "checkpoint");
+  }
+}
+
+TileSet rec_tiles(sp2_ctx* c, int j) {
+  Rec& r = c->recs[j];
+  TileSet t;
+  t.nnzb = r.nnzb;
+  t.brow = r.brow.as<int32_t>();
+  t.bcol = r.bcol.as<int32_t>();
+  t.slot = c->ident.as<int32_t>();
+  t.rowptr = r.rowptr.as<int32_t>();
+  return t;
+}
+
+bool use_tc(const sp2_ctx* c, int i) {
+  const sp2_params& p = c->prm;
+  if (p.precision != SP2_PREC_SPLIT16) return false;
+  if (i < p.mixed_from) return false;
+  if (p.mixed_until > 0 && i > p.mixed_until) return false;
+  return true;
+}
+
+// S = X~^2 on the output tiles with the tcgen05 FP16-slice kernel, fused epilogue.
+void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool) {
+  const int k = c->prm.slices;
+  const size_t blk = slice_block_bytes(k);
+  const int64_t pool_tiles = (int64_t)(c->pool[c->cur].cap / ((size_t)TE * 8));
+  c->ensure(c->slices, (size_t)pool_tiles * 2 * blk);
+  c->ensure(c->zero16, blk);
+  c->ck(launch_zero_half(c->zero16.p, (int64_t)k * TE, c->st), "zero block");
+  c->ck(launch_make_slices(c->X, c->pool[c->cur].as<double>(), c->slices.p, k, c->errflag.as<int32_t>(), c->st),
+        "make slices");
+  const int nsr = (c->nb + 3) / 4;
+  c->ensure(c->sbits, (size_t)nsr * c->words * 4);
+  c->ck(launch_super_bits(c->fp, c->nb, nsr, c->sbits.as<uint32_t>(), c->st), "super bits");
+  const int64_t npair = (int64_t)nsr * nsr;
+  c->ensure(c->sflag, (size_t)npair * 4);
+  c->ensure(c->spos, (size_t)npair * 4);
+  c->ensure(c->scantmp, scan_tmp_bytes(npair) + 4096);
+  c->ck(launch_super_flags(c->o_bits.as<uint32_t>(), c->nb, c->words, nsr, c->sflag.as<int32_t>(), c->st),
+        "super flags");
+  c->ck(launch_scan_i32(c->sflag.as<int32_t>(), c->spos.as<int32_t>(), npair, c->dcnt.as<int32_t>(), c->scantmp.p,
+                        c->st),
+        "scan");
+  const int64_t nsuper = read_count(c, c->dcnt.as<int32_t>());
+  c->ensure(c->slist, (size_t)std::max<int64_t>(nsuper, 1) * 4);
+  c->ck(launch_super_fill(c->sflag.as<int32_t>(), c->spos.as<int32_t>(), npair, nsr, c->slist.as<int32_t>(), c->st),
+        "super fill");
+  TcLaunch L;
+  L.X = &c->fp;
+  L.sbits = c->sbits.as<uint32_t>();
+  L.slices = c->slices.p;
+  L.zero = c->zero16.p;
+  L.zpool = c->pool[c->cur].as<double>();
+  L.obits = c->o_bits.as<uint32_t>();
+  L.orowptr = c->o_rowptr.as<int32_t>();
+  L.list = c->slist.as<int32_t>();
+  L.nsuper = nsuper;
+  L.opool = outpool;
+  L.part = partials(c);
+  L.c0 = c0; L.c1 = c1; L.c2 = c2;
+  L.n = c->n; L.nb = c->nb; L.nsr = nsr; L.k = k;
+  L.err = c->errflag.as<int32_t>();
+  c->ck(cudaEventRecord(c->evs0, c->st), "event");
+  c->ck(launch_square_tc(L, c->st), "square tc");
+  c->ck(cudaEventRecord(c->evs1, c->st), "event");
 }
 
 int fill_stats_sched(sp2_ctx* c) {
@@ -554,6 +671,8 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       S.prec_hist[i] = -1;
     }
     const long long launches0 = g_launches;
+    c->ensure(c->errflag, 16);
+    c->ck(cudaMemsetAsync(c->errflag.p, 0, 16, c->st), "memset");
     c->ck(cudaEventRecord(c->ev0, c->st), "event");
     // Algorithm 1: X_0 on F's pattern, then X~_0 = trunc(X_0, tau_0)
     const int64_t nF = c->F.nnzb;
@@ -565,6 +684,8 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
     c->cur = 0;
     truncate_into_X(c, c->F, c->p_n2.as<double>(), sch.tau[0]);
     S.nnzb_hist[0] = c->X.nnzb;
+    free_recs(c);
+    record(c, 0);
     std::vector<double> ev, tv;
     int n_out = -1;
     bool converged = false;
@@ -603,13 +724,23 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       sa.c0 = c0; sa.c1 = c1; sa.c2 = c2;
       sa.n = c->n; sa.nb = c->nb;
       sa.part = partials(c);
-      c->ck(cudaEventRecord(c->evs0, c->st), "event");
-      c->ck(launch_square_f64(sa, c->st), "square f64");
-      c->ck(cudaEventRecord(c->evs1, c->st), "event");
+      const bool tc = use_tc(c, i);
+      if (tc) {
+        square_tc(c, c0, c1, c2, sa.outpool);
+      } else {
+        c->ck(cudaEventRecord(c->evs0, c->st), "event");
+        c->ck(launch_square_f64(sa, c->st), "square f64");
+        c->ck(cudaEventRecord(c->evs1, c->st), "event");
+      }
       c->ensure(c->dsc, sizeof(StepScalars));
       c->ck(launch_reduce_step(sa.part, nout, c->dsc.as<StepScalars>(), c->st), "reduce");
       c->ck(cudaMemcpyAsync(c->h_sc, c->dsc.p, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->st), "d2h");
+      c->ck(cudaMemcpyAsync(c->h_cnt + 2, c->errflag.p, 4, cudaMemcpyDeviceToHost, c->st), "d2h");
       c->sync();
+      if (c->h_cnt[2] & 1) {
+        c->last_error = "tensor-core square: a bounded wait timed out";
+        throw Fail{SP2_ERR_TIMEOUT};
+      }
       float ms = 0.f;
       c->ck(cudaEventElapsedTime(&ms, c->evs0, c->evs1), "elapsed");
       S.square_ms += ms;
@@ -622,7 +753,7 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       tv.push_back(tj);
       S.e[j] = ej;
       S.t[j] = tj;
-      S.prec_hist[j] = SP2_PREC_FP64;
+      S.prec_hist[j] = tc ? SP2_PREC_SPLIT16 : SP2_PREC_FP64;
       bool stop = false;
       if (c->prm.stop == SP2_STOP_PARAMETERLESS) {
         stop = j >= std::max(sch.n_min, 2) && sch.p[j] != sch.p[j - 1] && ev[j] > C_STOP * (ev[j - 2] * ev[j - 2]);
@@ -635,6 +766,7 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       truncate_into_X(c, c->out, c->p_n2.as<double>(), sch.tau[i]);
       c->cur = nxt;
       S.nnzb_hist[i] = c->X.nnzb;
+      record(c, i);
     }
     // D = X~_n: contiguous copy for the caller's view
     c->d_nnzb = c->X.nnzb;
@@ -705,7 +837,196 @@ int sp2_copy_D(sp2_ctx* c, int32_t* brow, int32_t* bcol, double* val, int64_t ca
 
 int sp2_backward(sp2_ctx* c, const sp2_bsr* W, sp2_bsr* dF) {
   if (!c || !W || !dF) return SP2_ERR_INVALID_ARG;
-  return SP2_ERR_STATE;
+  if (W->b != TB || W->n != c->n || W->nnzb < 0 || (W->nnzb > 0 && (!W->brow || !W->bcol || !W->val)))
+    return SP2_ERR_INVALID_ARG;
+  if (!c->have_D || !c->prm.record_masks) return SP2_ERR_STATE;
+  const int n = c->stats.n;
+  if (n < 0 || (int)c->recs.size() < n + 1) return SP2_ERR_STATE;
+  try {
+    c->ck(cudaEventRecord(c->ev0, c->st), "event");
+    const Schedule& sch = c->sch;
+    const int k = c->prm.ckpt_every;
+    // W -> device, validated like F (diagonal tiles not required)
+    const int64_t nw = W->nnzb;
+    const cudaMemcpyKind kind = W->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+    c->ensure(c->w_brow, (size_t)std::max<int64_t>(nw, 1) * 4);
+    c->ensure(c->w_bcol, (size_t)std::max<int64_t>(nw, 1) * 4);
+    c->ensure(c->w_rowptr, (size_t)(c->nb + 1) * 4);
+    c->ensure(c->w_pool, (size_t)std::max<int64_t>(nw, 1) * TE * 8);
+    if (nw > 0) {
+      c->ck(cudaMemcpyAsync(c->w_brow.p, W->brow, nw * 4, kind, c->st), "copy W");
+      c->ck(cudaMemcpyAsync(c->w_bcol.p, W->bcol, nw * 4, kind, c->st), "copy W");
+      c->ck(cudaMemcpyAsync(c->w_pool.p, W->val, (size_t)nw * TE * 8, kind, c->st), "copy W");
+      c->ensure(c->dcnt, 16);
+      c->ck(launch_check_pattern(c->w_brow.as<int32_t>(), c->w_bcol.as<int32_t>(), nw, c->nb, c->w_pool.as<double>(),
+                                 c->n, c->dcnt.as<int32_t>(), c->st),
+            "check W");
+      c->ck(cudaMemcpyAsync(c->h_cnt, c->dcnt.p, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
+      c->sync();
+      if (c->h_cnt[0] & 1) throw Fail{SP2_ERR_PATTERN};
+      if (c->h_cnt[0] & 2) throw Fail{SP2_ERR_NONFINITE};
+    }
+    c->ck(launch_rowptr_from_brow(c->w_brow.as<int32_t>(), nw, c->nb, c->w_rowptr.as<int32_t>(), c->st), "rowptr");
+    int64_t mx = std::max<int64_t>(nw, c->F.nnzb);
+    for (int j = 0; j <= n; ++j) mx = std::max(mx, c->recs[j].nnzb);
+    ensure_ident(c, mx);
+    TileSet Wt;
+    Wt.nnzb = nw;
+    Wt.brow = c->w_brow.as<int32_t>();
+    Wt.bcol = c->w_bcol.as<int32_t>();
+    Wt.slot = c->ident.as<int32_t>();
+    Wt.rowptr = c->w_rowptr.as<int32_t>();
+    // G_n = W on the tiles of D = X~_n (dL/dD for L = trace(D W), W symmetric)
+    int gcur = 0;
+    {
+      TileSet tn = rec_tiles(c, n);
+      c->ensure(c->gpool[0], (size_t)std::max<int64_t>(tn.nnzb, 1) * TE * 8);
+      c->ck(launch_place(Wt, c->w_pool.as<double>(), tn, c->gpool[0].as<double>(), 1.0, 1, c->st), "place W");
+    }
+    int i = n;
+    while (i >= 1) {
+      const int cp = ((i - 1) / k) * k;  // checkpoint holding X~_cp
+      if (!c->recs[cp].has_val) throw Fail{SP2_ERR_STATE};
+      // recompute X~_{cp+1} .. X~_{i-1} on their recorded tiles (no truncation needed)
+      const int len = i - cp;             // seg[0] = X~_cp, ..., seg[len-1] = X~_{i-1}
+      if ((int)c->seg.size() < len) c->seg.resize(len);
+      std::vector<const double*> vals(len);
+      vals[0] = c->recs[cp].val.as<double>();
+      for (int j = cp + 1; j < i; ++j) {
+        TileSet prev = rec_tiles(c, j - 1), cur = rec_tiles(c, j);
+        build_full(c, prev, c->fpB, c->fpB_bits, c->fpB_rowptr, c->fpB_col, c->fpB_ref);
+        Buf& dst = c->seg[j - cp];
+        c->ensure(dst, (size_t)std::max<int64_t>(cur.nnzb, 1) * TE * 8);
+        ensure_partials(c, std::max<int64_t>(cur.nnzb, 1));
+        double c0, c1, c2;
+        coeffs(sch.p[j], sch.alpha[j], c0, c1, c2);
+        SquareArgs sa;
+        sa.A = &c->fpB; sa.apool = vals[j - 1 - cp];
+        sa.B = &c->fpB; sa.bpool = vals[j - 1 - cp];
+        sa.sym_sum = false;
+        sa.Z = &c->fpB; sa.zpool = vals[j - 1 - cp];
+        sa.out = &cur; sa.outpool = dst.as<double>();
+        sa.c0 = c0; sa.c1 = c1; sa.c2 = c2;
+        sa.n = c->n; sa.nb = c->nb;
+        sa.part = partials(c);
+        c->ck(launch_square_f64(sa, c->st), "replay square");
+        vals[j - cp] = dst.as<double>();
+      }
+      // reverse steps i .. cp+1:  G_{j-1} = mask_{j-1}( c1 G_j + c2 (G_j X~_{j-1} + X~_{j-1} G_j) )
+      for (; i > cp; --i) {
+        TileSet tg = rec_tiles(c, i), tp = rec_tiles(c, i - 1);
+        build_full(c, tg, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
+        build_full(c, tp, c->fpB, c->fpB_bits, c->fpB_rowptr, c->fpB_col, c->fpB_ref);
+        const int nxt = 1 - gcur;
+        c->ensure(c->gpool[nxt], (size_t)std::max<int64_t>(tp.nnzb, 1) * TE * 8);
+        ensure_partials(c, std::max<int64_t>(tp.nnzb, 1));
+        double c0, c1, c2;
+        coeffs(sch.p[i], sch.alpha[i], c0, c1, c2);
+        SquareArgs sa;
+        sa.A = &c->fp; sa.apool = c->gpool[gcur].as<double>();
+        sa.B = &c->fpB; sa.bpool = vals[i - 1 - cp];
+        sa.sym_sum = true;
+        sa.Z = &c->fp; sa.zpool = c->gpool[gcur].as<double>();
+        sa.out = &tp; sa.outpool = c->gpool[nxt].as<double>();
+        sa.c0 = 0.0; sa.c1 = c1; sa.c2 = c2;
+        sa.n = c->n; sa.nb = c->nb;
+        sa.part = partials(c);
+        c->ck(launch_square_f64(sa, c->st), "adjoint step");
+        gcur = nxt;
+      }
+    }
+    // X_0 = (lmax I - F) / w:  dL/dF = -G_0 / w on F's tiles (0 where X~_0 dropped a tile)
+    TileSet t0 = rec_tiles(c, 0);
+    c->ensure(c->dF, (size_t)std::max<int64_t>(c->F.nnzb, 1) * TE * 8);
+    c->ck(launch_place(t0, c->gpool[gcur].as<double>(), c->F, c->dF.as<double>(), -1.0 / (sch.lmax - sch.lmin), 0,
+                       c->st),
+          "dF");
+    c->ck(cudaEventRecord(c->ev1, c->st), "event");
+    c->sync();
+    float ms = 0.f;
+    c->ck(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "elapsed");
+    c->backward_ms = ms;
+    c->stats.backward_ms = ms;
+    dF->n = c->n;
+    dF->b = TB;
+    dF->nnzb = c->F.nnzb;
+    dF->brow = c->F.brow;
+    dF->bcol = c->F.bcol;
+    dF->val = c->dF.as<double>();
+    dF->on_device = 1;
+  } catch (const Fail& f) {
+    if (f.code == SP2_ERR_CUDA || f.code == SP2_ERR_OOM) fprintf(stderr, "sp2_backward: %s\n", c->last_error.c_str());
+    return f.code;
+  }
+  return SP2_OK;
+}
+
+int sp2_truncate(const sp2_bsr* X, double tau, int32_t mode, int64_t frobinf_part, int32_t* keep,
+                 void* cuda_stream) {
+  if (!X || !keep || X->b != TB || X->n <= 0 || X->nnzb < 0 || !(tau >= 0.0) || !std::isfinite(tau))
+    return SP2_ERR_INVALID_ARG;
+  if (X->nnzb > 0 && (!X->brow || !X->bcol || !X->val)) return SP2_ERR_INVALID_ARG;
+  if (mode != SP2_TRUNC_FROBENIUS && mode != SP2_TRUNC_FROBINF) return SP2_ERR_INVALID_ARG;
+  if (mode == SP2_TRUNC_FROBINF && (frobinf_part < TB || frobinf_part % TB)) return SP2_ERR_INVALID_ARG;
+  const int64_t nb64 = (X->n + TB - 1) / TB;
+  if (nb64 > 65535) return SP2_ERR_INVALID_ARG;
+  if (X->nnzb == 0) return SP2_OK;
+  cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
+  const int nb = (int)nb64;
+  const int64_t nnzb = X->nnzb;
+  const int64_t part_tiles = std::max<int64_t>(1, frobinf_part / TB);
+  void *dbrow = nullptr, *dbcol = nullptr, *dval = nullptr, *dn2 = nullptr, *work = nullptr, *dkeep = nullptr;
+  int rc = SP2_OK;
+  auto get = [&](void** p, size_t bytes) {
+    if (cudaMallocAsync(p, std::max<size_t>(bytes, 256), st) != cudaSuccess) {
+      cudaGetLastError();
+      rc = SP2_ERR_OOM;
+      return false;
+    }
+    return true;
+  };
+  const bool dev = X->on_device != 0;
+  const int32_t* brow = X->brow;
+  const int32_t* bcol = X->bcol;
+  const double* val = X->val;
+  do {
+    if (!dev) {
+      if (!get(&dbrow, nnzb * 4) || !get(&dbcol, nnzb * 4) || !get(&dval, (size_t)nnzb * TE * 8)) break;
+      if (cudaMemcpyAsync(dbrow, X->brow, nnzb * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(dbcol, X->bcol, nnzb * 4, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+          cudaMemcpyAsync(dval, X->val, (size_t)nnzb * TE * 8, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        rc = SP2_ERR_CUDA;
+        break;
+      }
+      brow = static_cast<int32_t*>(dbrow);
+      bcol = static_cast<int32_t*>(dbcol);
+      val = static_cast<double*>(dval);
+    }
+    if (!get(&dn2, nnzb * 8) || !get(&work, trunc_work_bytes(nnzb, nb, part_tiles))) break;
+    int32_t* kout = keep;
+    if (!dev) {
+      if (!get(&dkeep, nnzb * 4)) break;
+      kout = static_cast<int32_t*>(dkeep);
+    }
+    TileSet ts;
+    ts.nnzb = nnzb;
+    ts.brow = const_cast<int32_t*>(brow);
+    ts.bcol = const_cast<int32_t*>(bcol);
+    ts.slot = nullptr;
+    if (launch_tile_norms(val, nnzb, static_cast<double*>(dn2), st) != cudaSuccess ||
+        launch_truncate(ts, static_cast<double*>(dn2), nb, tau, mode, part_tiles, work, kout, st) != cudaSuccess) {
+      rc = SP2_ERR_CUDA;
+      break;
+    }
+    if (!dev && cudaMemcpyAsync(keep, dkeep, nnzb * 4, cudaMemcpyDeviceToHost, st) != cudaSuccess) {
+      rc = SP2_ERR_CUDA;
+      break;
+    }
+  } while (false);
+  for (void* p : {dbrow, dbcol, dval, dn2, work, dkeep})
+    if (p) cudaFreeAsync(p, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess && rc == SP2_OK) rc = SP2_ERR_CUDA;
+  return rc;
 }
 
 int sp2_get_stats(const sp2_ctx* c, sp2_stats* s) {
@@ -716,6 +1037,7 @@ int sp2_get_stats(const sp2_ctx* c, sp2_stats* s) {
 
 void sp2_destroy(sp2_ctx* c) {
   if (!c) return;
+  free_recs(c);
   for (Buf* b : c->bufs) {
     c->al.put(b->p);
     b->p = nullptr;

@@ -100,14 +100,45 @@ size_t trunc_work_bytes(int64_t nnzb, int nb, int64_t part_tiles);
 cudaError_t launch_truncate(const TileSet& x, const double* n2, int nb, double tau, int mode, int64_t part_tiles,
                             void* work, int32_t* keep, cudaStream_t st);
 
+cudaError_t launch_tile_norms(const double* val, int64_t nnzb, double* n2, cudaStream_t st);
+
 // compact.cu
 cudaError_t launch_compact(const TileSet& in, const int32_t* keep, int nb, TileSet& out, int32_t* count_dev,
                            void* scan_tmp, int32_t* scan_buf, cudaStream_t st);
 cudaError_t launch_gather_tiles(const TileSet& s, const double* pool, double* dst, cudaStream_t st);
 cudaError_t launch_copy_index(const TileSet& s, int32_t* brow, int32_t* bcol, cudaStream_t st);
-cudaError_t launch_mask_to_pattern(const TileSet& src, const double* srcpool, const FullPattern& dstpat,
-                                   const TileSet& dst, double* dstpool, double scale, cudaStream_t st);
-cudaError_t launch_sym_into(const TileSet& w, const double* wpool, const FullPattern& pat, const TileSet& dst,
-                            double* dstpool, cudaStream_t st);
+// dst tiles := scale * the tile of `src` at the same (I, J), 0 when absent; src
+// needs rowptr; sym_diag symmetrises diagonal tiles.
+cudaError_t launch_place(const TileSet& src, const double* spool, const TileSet& dst, double* dpool, double scale,
+                         int sym_diag, cudaStream_t st);
+cudaError_t launch_iota(int32_t* p, int64_t n, cudaStream_t st);
+
+// square_tc.cu: tcgen05 FP16-slice product (see the file header)
+struct TcLaunch {
+  const FullPattern* X;      // pattern of X~ (values: zpool, slices by slot)
+  const uint32_t* sbits;     // super-row bitmaps
+  const void* slices;        // FP16 slices [slot][2][k][1024]
+  const void* zero;          // k * 1024 FP16 zeros
+  const double* zpool;
+  const uint32_t* obits;     // output pattern bitmap
+  const int32_t* orowptr;
+  const int32_t* list;       // active super-tiles
+  int64_t nsuper;
+  double* opool;
+  Partials part;
+  double c0, c1, c2;
+  int64_t n;
+  int nb, nsr, k;
+  int32_t* err;
+};
+size_t slice_block_bytes(int k);
+cudaError_t launch_make_slices(const TileSet& x, const double* pool, void* slices, int k, int32_t* err,
+                               cudaStream_t st);
+cudaError_t launch_zero_half(void* p, int64_t n, cudaStream_t st);
+cudaError_t launch_super_bits(const FullPattern& fp, int nb, int nsr, uint32_t* sb, cudaStream_t st);
+cudaError_t launch_super_flags(const uint32_t* obits, int nb, int words, int nsr, int32_t* flag, cudaStream_t st);
+cudaError_t launch_super_fill(const int32_t* flag, const int32_t* pos, int64_t n, int nsr, int32_t* list,
+                              cudaStream_t st);
+cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st);
 
 }  // namespace sp2

@@ -216,9 +216,32 @@ __global__ void k_mark(const int32_t* __restrict__ brow, const int32_t* __restri
   keep[t] = drop ? 0 : 1;
 }
 
+// ||tile||_F^2 of contiguous tiles (fixed order: 4 strided partial sums per
+// thread, then a fixed tree), one CTA of 256 threads per tile.
+__global__ void __launch_bounds__(256) k_tile_norms(const double* __restrict__ val, double* n2) {
+  const int64_t t = blockIdx.x;
+  const double* x = val + t * TE;
+  double a = 0.0;
+  for (int q = threadIdx.x; q < TE; q += 256) a += x[q] * x[q];
+  __shared__ double red[256];
+  red[threadIdx.x] = a;
+  __syncthreads();
+  for (int h = 128; h > 0; h >>= 1) {
+    if ((int)threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) n2[t] = red[0];
+}
+
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t launch_tile_norms(const double* val, int64_t nnzb, double* n2, cudaStream_t st) {
+  if (nnzb == 0) return cudaSuccess;
+  { ++g_launches; k_tile_norms<<<(unsigned)nnzb, 256, 0, st>>>(val, n2); }
+  return cudaGetLastError();
+}
 
 size_t trunc_work_bytes(int64_t nnzb, int nb, int64_t part_tiles) {
   const int nsb = (int)((nb + part_tiles - 1) / part_tiles);

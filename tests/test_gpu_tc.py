@@ -1,0 +1,86 @@
+"""Tensor-core (tcgen05) FP16-slice path against the CPU oracle and the FP64 GPU
+path.  Target tolerance of the mixed path: ||D - D_oracle||_F <= 1e-6 with four
+slices; the two- and three-slice forms are measured and reported."""
+import numpy as np
+import pytest
+
+from synth import dense_gapped, from_dense, make_config
+from tests.helpers import run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+MIXED_TOL = 1e-6
+
+
+def _err(g, o):
+    return float(np.linalg.norm(g["D"] - o.D))
+
+
+@pytest.mark.parametrize("key", [1, "2s", "4s"])
+def test_split16_k4_meets_tolerance(key):
+    c = make_config(key)
+    kw = dict(stop=c["stop"])
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], precision="split16", slices=4, **kw)
+    err = _err(g, o)
+    print(f"config {key}: split16 k=4 ||D-Dref||_F = {err:.3e}, n = {g['stats']['n']} (oracle {o.n})")
+    assert g["stats"]["prec_hist"][0] == 1
+    assert err <= MIXED_TOL
+    assert abs(g["stats"]["n"] - o.n) <= 1
+    n = g["D"].shape[0]
+    assert abs(np.trace(g["D"]) - c["nocc"]) <= 1e-6 * max(1.0, np.sqrt(n))
+
+
+def test_split16_first_square_matches_fp64_closely():
+    # one step only: e_0, t_0 come from S = X~_0^2; slices on a 2^-43 grid
+    c = make_config("2s")
+    a = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], n_max_cap=1)
+    b = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], n_max_cap=1, precision="split16", slices=4)
+    ea, eb = a["stats"]["e"], b["stats"]["e"]
+    np.testing.assert_allclose(eb, ea, rtol=1e-9)
+    np.testing.assert_allclose(b["stats"]["t"], a["stats"]["t"], rtol=1e-9)
+    assert np.linalg.norm(a["D"] - b["D"]) < 1e-9
+
+
+@pytest.mark.parametrize("k", [2, 3])
+def test_split16_fewer_slices_reported(k):
+    c = make_config("2s")
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"])
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], precision="split16", slices=k)
+    err = _err(g, o)
+    print(f"split16 k={k}: ||D-Dref||_F = {err:.3e}")
+    assert np.isfinite(err) and err < 1.0
+
+
+@pytest.mark.parametrize("n", [33, 100, 129, 300])
+def test_split16_ragged_sizes(n):
+    d = dense_gapped(n, n // 3, (-2.0, -0.3), (0.4, 2.0), seed=100 + n)
+    o = run_oracle(d["F"], d["nocc"], d["homo_ub"], d["lumo_lb"], 0.0, stop="idempotency", idem_tol=1e-11)
+    g = run_gpu(d["F"], d["nocc"], d["homo_ub"], d["lumo_lb"], 0.0, stop="idempotency", idem_tol=1e-11,
+                precision="split16", slices=4)
+    err = _err(g, o)
+    assert err <= MIXED_TOL, err
+
+
+def test_split16_then_fp64_schedule():
+    # mixed precision schedule: tensor cores up to iteration 8, FP64 afterwards
+    c = make_config("2s")
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"])
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], precision="split16", slices=4,
+                mixed_until=8)
+    ph = g["stats"]["prec_hist"]
+    assert ph[0] == 1 and ph[-1] == 0
+    assert _err(g, o) <= MIXED_TOL
+
+
+def test_split16_block_diagonal_sparse_supertiles():
+    a = dense_gapped(200, 90, (-1.0, -0.4), (0.4, 1.0), seed=5)["F"]
+    b = dense_gapped(190, 80, (-1.0, -0.4), (0.4, 1.0), seed=6)["F"]
+    F = np.zeros((390, 390))
+    F[:200, :200] = a
+    F[200:, 200:] = b
+    Fb = from_dense(F)
+    o = run_oracle(Fb, 170, -0.4, 0.4, 0.0, stop="idempotency")
+    g = run_gpu(Fb, 170, -0.4, 0.4, 0.0, stop="idempotency", precision="split16", slices=4)
+    assert _err(g, o) <= MIXED_TOL
+    assert list(zip(g["brow"].tolist(), g["bcol"].tolist())) == sorted(o.kept[o.n])

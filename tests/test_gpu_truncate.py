@@ -1,0 +1,71 @@
+"""Truncation step (Eq. (8)) through sp2_truncate against the oracle's selection:
+bit-exact keep flags, including exact ties, tau = 0 and the two extremes."""
+import numpy as np
+import pytest
+
+import oracle.sp2_oracle as O
+from synth import BlockSparse, from_dense, to_dense
+
+pytestmark = pytest.mark.gpu
+
+
+def _decaying(n, seed, ties=False):
+    rng = np.random.default_rng(seed)
+    A = rng.standard_normal((n, n))
+    A = 0.5 * (A + A.T)
+    d = np.abs(np.subtract.outer(np.arange(n), np.arange(n)))
+    A *= np.exp(-d / 40.0)
+    X = from_dense(A, keep_zero_tiles=True)
+    if ties:
+        # several tiles with bit-identical values (equal norms): the index decides
+        off = np.nonzero(X.brow != X.bcol)[0]
+        src = X.val[off[3]].copy()
+        for k in off[5:40:3]:
+            X.val[k] = src * 1e-3
+    return X
+
+
+def _oracle_keep(X, tau, mode, part):
+    Xd = to_dense(X)
+    pattern = set(zip(X.brow.tolist(), X.bcol.tolist()))
+    _, kept, _ = O.truncate_select(Xd, tau, mode, part=part, pattern=pattern)
+    ks = set(kept)
+    return np.array([1 if (i, j) in ks else 0 for i, j in zip(X.brow.tolist(), X.bcol.tolist())], np.int32)
+
+
+@pytest.mark.parametrize("mode,part", [("frobenius", 4096), ("frobinf", 64), ("frobinf", 128)])
+@pytest.mark.parametrize("tau", [0.0, 1e-6, 1e-3, 0.1])
+@pytest.mark.parametrize("ties", [False, True])
+def test_keep_flags_bit_exact(mode, part, tau, ties):
+    import paper_1909_12533_gb300 as sp2
+    X = _decaying(331, 17, ties)      # 11 tile rows, ragged tail of 11
+    g = sp2.sp2_truncate(X, tau, mode, part)
+    o = _oracle_keep(X, tau, mode, part)
+    assert np.array_equal(g, o), np.nonzero(g != o)
+
+
+def test_zero_tiles_and_extremes():
+    import paper_1909_12533_gb300 as sp2
+    X = _decaying(200, 3)
+    X.val[2] = 0.0
+    X.val[7] = 0.0
+    keep = sp2.sp2_truncate(X, 0.0, "frobenius")
+    assert keep.sum() == X.nnzb - 2 and keep[2] == 0 and keep[7] == 0
+    assert sp2.sp2_truncate(X, 1e6, "frobenius").sum() == 0          # everything fits
+    assert sp2.sp2_truncate(X, 1e-300, "frobenius").sum() == X.nnzb - 2
+
+
+def test_device_input_matches_host_input():
+    import torch
+    import paper_1909_12533_gb300 as sp2
+    X = _decaying(480, 9)
+
+    class T:
+        n = X.n
+        brow = torch.from_numpy(X.brow).cuda()
+        bcol = torch.from_numpy(X.bcol).cuda()
+        val = torch.from_numpy(X.val).cuda()
+
+    kd = sp2.sp2_truncate(T, 1e-4, "frobinf", 128).cpu().numpy()
+    kh = sp2.sp2_truncate(X, 1e-4, "frobinf", 128)
+    assert np.array_equal(kd, kh)
