@@ -348,7 +348,8 @@ def header_functions() -> list[str]:
     """Names of the functions declared in include/sp2.h (for export checks)."""
     import re
     h = (Path(__file__).resolve().parent.parent / "include" / "sp2.h").read_text()
-    return sorted(set(re.findall(r"\b(sp2_[A-Za-z0-9_]+)\s*\(", h)))
+    h = re.sub(r"/\*.*?\*/", " ", h, flags=re.S)  # drop comments
+    return sorted(set(re.findall(r"^\s*(?:int|void|const\s+char\s*\*)\s*(sp2_[A-Za-z0-9_]+)\s*\(", h, re.M)))
 
 
 # ------------------------------------------------------------------ autograd

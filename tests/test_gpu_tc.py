@@ -39,7 +39,8 @@ def test_split16_first_square_matches_fp64_closely():
     ea, eb = a["stats"]["e"], b["stats"]["e"]
     np.testing.assert_allclose(eb, ea, rtol=1e-9)
     np.testing.assert_allclose(b["stats"]["t"], a["stats"]["t"], rtol=1e-9)
-    assert np.linalg.norm(a["D"] - b["D"]) < 1e-9
+    # 5.9M elements, each within ~1e-12 (2^-44 grid, FP32-exact groups)
+    assert np.linalg.norm(a["D"] - b["D"]) < 1e-8
 
 
 @pytest.mark.parametrize("k", [2, 3])
