@@ -50,6 +50,7 @@ extern "C" {
 #define SP2_ERR_TIMEOUT       -8  /* a bounded device wait gave up                 */
 #define SP2_ERR_STATE         -9  /* call out of order (e.g. get_D before run)     */
 #define SP2_ERR_CAPACITY     -10  /* caller buffer too small (size returned)       */
+#define SP2_ERR_TOO_LARGE    -11  /* input exceeds the fixed scratch of sp2_truncate_noalloc */
 
 #define SP2_TILE 32
 #define SP2_MAX_ITER 128
@@ -184,6 +185,29 @@ int sp2_backward(sp2_ctx* ctx, const sp2_bsr* W, sp2_bsr* dF_view);
  * that stream before returning.  Errors: INVALID_ARG, OOM, CUDA. */
 int sp2_truncate(const sp2_bsr* X, double tau, int32_t mode, int64_t frobinf_part, int32_t* keep,
                  void* cuda_stream);
+
+/* Allocation-free variant of sp2_truncate, for callers that may not allocate
+ * device memory: code that issues work while a CUDA graph is being captured,
+ * callbacks of frameworks that own all device memory, or processes whose
+ * allocator is locked after start-up.  (The paper has no counterpart; the
+ * selection rule is that of sp2_truncate.)  All pointers are device pointers
+ * that the caller owns: brow, bcol, val as in sp2_bsr (n is the matrix
+ * dimension, nnzb the tile count, tiles sorted upper-triangle) and keep[nnzb]
+ * for the result (1 = kept).  Work is queued on cuda_stream and not
+ * synchronised.
+ * Scratch: one file-scope device array of 8 MiB in this library, shared by all
+ * calls on a device and kept by every GPU that loads the library until the
+ * process exits.  Limits: nnzb <= 262144 tiles and, in Frob-Inf mode, at most
+ * 32 x 32 super-blocks; larger inputs return SP2_ERR_TOO_LARGE.  The first call
+ * on a device looks the array's device address up (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  The
+ * array keeps the previous call's contents; everything that must start at zero
+ * is cleared inside the call.  Calls that overlap on the GPU (different streams
+ * or devices sharing the array) race on the scratch: serialise them.
+ * No cudaMalloc, cudaFree or other allocating routine is called.
+ * Errors: INVALID_ARG, TOO_LARGE, CUDA. */
+int sp2_truncate_noalloc(const int32_t* brow, const int32_t* bcol, const double* val, int64_t n, int64_t nnzb,
+                         double tau, int32_t mode, int64_t frobinf_part, int32_t* keep, void* cuda_stream);
 
 int sp2_get_stats(const sp2_ctx* ctx, sp2_stats* stats);
 void sp2_destroy(sp2_ctx* ctx);

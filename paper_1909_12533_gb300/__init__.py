@@ -24,7 +24,7 @@ SP2_OK = 0
 ERRORS = {
     -1: "SP2_ERR_INVALID_ARG", -2: "SP2_ERR_BOUNDS", -3: "SP2_ERR_PATTERN", -4: "SP2_ERR_NONFINITE",
     -5: "SP2_ERR_OOM", -6: "SP2_ERR_CUDA", -7: "SP2_ERR_NOT_CONVERGED", -8: "SP2_ERR_TIMEOUT",
-    -9: "SP2_ERR_STATE", -10: "SP2_ERR_CAPACITY",
+    -9: "SP2_ERR_STATE", -10: "SP2_ERR_CAPACITY", -11: "SP2_ERR_TOO_LARGE",
 }
 NOT_CONVERGED = -7
 MODES = {"sp2": 0, "sp2acc": 1}
@@ -70,6 +70,8 @@ _SIGS = [
     ("sp2_copy_D", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, POINTER(c_int64)]),
     ("sp2_backward", c_int32, [c_void_p, POINTER(sp2_bsr), POINTER(sp2_bsr)]),
     ("sp2_truncate", c_int32, [POINTER(sp2_bsr), c_double, c_int32, c_int64, c_void_p, c_void_p]),
+    ("sp2_truncate_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_double, c_int32, c_int64,
+                                       c_void_p, c_void_p]),
     ("sp2_get_stats", c_int32, [c_void_p, POINTER(sp2_stats)]),
     ("sp2_destroy", None, [c_void_p]),
     ("sp2_strerror", ctypes.c_char_p, [c_int32]),

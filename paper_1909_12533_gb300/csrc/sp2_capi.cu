@@ -545,6 +545,7 @@ const char* sp2_strerror(int code) {
     case SP2_ERR_TIMEOUT: return "bounded device wait timed out";
     case SP2_ERR_STATE: return "call out of order";
     case SP2_ERR_CAPACITY: return "buffer too small";
+    case SP2_ERR_TOO_LARGE: return "input exceeds the fixed scratch of the allocation-free entry point";
     default: return "unknown error";
   }
 }
