@@ -4,6 +4,9 @@
 Workload (default): the water-like Fock matrix with 1000 molecules, N = 24000,
 tile b = 32, tau = 1e-6, Frobenius truncation, parameterless stop.  It is a
 seeded synthetic stand-in for the paper's HF/3-21G water clusters.
+The headline path is the tcgen05 tensor-core square on four FP16 slices (the
+FP64 GPU path is timed once on the same workload for comparison, and the
+difference of the two D's is reported).
 A step is one full pass of the method: sp2_create from the device-resident F
 (Gershgorin bounds, schedule, X_0), then sp2_run (every iteration's symbolic
 square, tile products with the fused epilogue, reductions, stop test,
@@ -145,15 +148,43 @@ def run_reference(args):
     return 0
 
 
+def _tile_diff_norm(a, b, nb):
+    """||A - B||_F of two symmetric tile sets (brow, bcol, val) on the device;
+    tiles present in only one of them count in full; off-diagonal tiles twice."""
+    import torch
+    ka = a[0].long() * nb + a[1].long()
+    kb = b[0].long() * nb + b[1].long()
+    pos = torch.searchsorted(kb, ka).clamp(max=max(kb.numel() - 1, 0))
+    hit = kb[pos] == ka if kb.numel() else torch.zeros_like(ka, dtype=torch.bool)
+    wa = torch.where(a[0] == a[1], 1.0, 2.0).to(torch.float64)
+    wb = torch.where(b[0] == b[1], 1.0, 2.0).to(torch.float64)
+    da = a[2].clone()
+    da[hit] -= b[2][pos[hit]]
+    tot = (wa * (da * da).sum(dim=(1, 2))).sum()
+    inb = torch.zeros(kb.numel(), dtype=torch.bool, device=kb.device)
+    inb[pos[hit]] = True
+    tot += (wb[~inb] * (b[2][~inb] ** 2).sum(dim=(1, 2))).sum()
+    return float(tot.sqrt())
+
+
+def _trace(D, n):
+    import torch
+    d = D[0] == D[1]
+    idx = torch.arange(32, device=D[2].device)
+    diag = D[2][d][:, idx, idx]
+    return float(diag.sum())
+
+
 def main(argv=None) -> int:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2)
+    ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="water24k", choices=sorted(WORKLOADS))
-    ap.add_argument("--precision", default="fp64", choices=["fp64", "split16"])
+    ap.add_argument("--precision", default="split16", choices=["fp64", "split16"])
     ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--no-fp64-compare", action="store_true", help="skip the timed FP64 reference run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
@@ -163,7 +194,7 @@ def main(argv=None) -> int:
     import numpy as np
     import torch
     import paper_1909_12533_gb300 as sp2
-    from synth import make_config
+    from synth import from_dense, make_config
 
     rank, world, local = dist_env()
     torch.cuda.set_device(local)
@@ -174,8 +205,8 @@ def main(argv=None) -> int:
 
     wl = WORKLOADS[args.workload]
     c = make_config(wl["key"])
-    from synth import from_dense
     Fh = c["F"] if not isinstance(c["F"], np.ndarray) else from_dense(c["F"])
+    nb = Fh.nb
 
     class Dev:
         n = Fh.n
@@ -183,17 +214,18 @@ def main(argv=None) -> int:
         bcol = torch.from_numpy(Fh.bcol).cuda()
         val = torch.from_numpy(Fh.val).cuda()
 
-    prm = dict(stop=c["stop"], precision=args.precision, slices=args.slices)
     stream = torch.cuda.current_stream()
 
-    def step(F):
-        ctx = sp2.SP2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **prm)
+    def step(F, precision, keep_D=False):
+        ctx = sp2.SP2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision=precision,
+                      slices=args.slices)
         st = ctx.run()
+        D = ctx.D_device() if keep_D else None
         ctx.close()
-        return st
+        return st, D
 
     for _ in range(args.warmup):
-        step(Dev)
+        step(Dev, args.precision)
     torch.cuda.synchronize()
     if world > 1:
         torch.distributed.barrier()
@@ -203,7 +235,7 @@ def main(argv=None) -> int:
     e1 = torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     e0.record(stream)
-    stats = [step(Dev) for _ in range(args.steps)]
+    stats = [step(Dev, args.precision)[0] for _ in range(args.steps)]
     e1.record(stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
@@ -213,6 +245,7 @@ def main(argv=None) -> int:
     flops = sum(s["alg_flops"] for s in stats)
     sq_ms = sum(s["square_ms"] for s in stats)
     squares = sum(s["squares"] for s in stats)
+    hw = sum(s["tc_hw_flops"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
     t = torch.tensor([ms, flops], dtype=torch.float64, device="cuda")
     if world > 1:
@@ -225,12 +258,33 @@ def main(argv=None) -> int:
         ms_max, flops_all = ms, flops
     value = flops_all / (ms_max / 1e3) / 1e12
 
-    # end to end through the public API with host buffers (H2D of F and D2H of D timed)
+    # accuracy of this path, and the FP64 GPU path timed on the same workload
+    st_main, D_main = step(Dev, args.precision, keep_D=True)
+    fp64 = None
+    err = None
+    if args.precision != "fp64" and not args.no_fp64_compare:
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        st64, D64 = step(Dev, "fp64", keep_D=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        err = _tile_diff_norm(D_main, D64, nb)
+        fp64 = {"time_to_D_ms": ms64, "eff_tflops": st64["alg_flops"] / ms64 / 1e9, "iterations": st64["n"],
+                "steps": 1, "warmup": 0, "nnzb_final": st64["nnzb_final"],
+                "speedup_of_mixed": ms64 / (ms_max / args.steps)}
+    accuracy = {"D_minus_D_fp64_F": err, "trace_minus_nocc": _trace(D_main, Fh.n) - c["nocc"],
+                "idempotency_e_n": st_main["e"][st_main["n"]], "iterations": st_main["n"],
+                "ref": "FP64 GPU path (itself bit-for-bit parity-tested against the CPU oracle)"}
+
     e2e = None
     if not args.no_e2e:
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx = sp2.SP2(Fh, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **prm)
+        ctx = sp2.SP2(Fh, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision=args.precision,
+                      slices=args.slices)
         st = ctx.run()
         brow, bcol, val = ctx.D_host()
         ctx.close()
@@ -253,21 +307,26 @@ def main(argv=None) -> int:
                 "peak_source": "GB300 FP64 nominal 1.25 TFLOP/s (no FP64 tensor path); measured DFMA 1.19"}
     else:
         pk = peaks["bf16_tflops_sustained"]
+        hw_ach = hw / (sq_ms / 1e3) / 1e12 if sq_ms > 0 else 0.0
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                "traffic": None, "kernel": "k_square_split16",
-                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (FP16 runs at the BF16 rate)"}
-    s0 = stats[-1]
+                "traffic": None, "kernel": "k_square_tc<%d>" % args.slices,
+                "hw_achieved": hw_ach, "hw_frac": hw_ach / pk,
+                "note": "achieved/frac count algorithmic flops (2*32^3 per tile triplet); hw_* count the "
+                        "FP16 MMAs issued (%d slice pairs per triplet plus 128x128 super-tile padding)"
+                        % (args.slices * (args.slices + 1) // 2),
+                "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; FP16 = BF16 rate)"}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f16-split+f64",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f16x%d-split+f64" % args.slices,
         "data": "synthetic",
         "config": {"workload": wl["desc"], "precision": args.precision,
                    "slices": args.slices if args.precision == "split16" else None,
                    "l2": "inputs larger than L2 (F alone is %.0f MB)" % (Fh.val.nbytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
-        "time_to_D_ms": ms_max / args.steps, "iterations": s0["n"], "squares": s0["squares"],
-        "alg_flops_per_step": s0["alg_flops"], "nnzb_final": s0["nnzb_final"],
+        "time_to_D_ms": ms_max / args.steps, "iterations": stats[-1]["n"], "squares": stats[-1]["squares"],
+        "alg_flops_per_step": stats[-1]["alg_flops"], "nnzb_final": stats[-1]["nnzb_final"],
+        "accuracy": accuracy, "fp64_path": fp64,
         "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
     }
     if not args.no_cpu_baseline and world == 1:

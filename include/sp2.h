@@ -130,6 +130,8 @@ typedef struct {
   int32_t prec_hist[SP2_MAX_ITER]; /* precision of the square that produced e_j         */
   int64_t kernel_launches;        /* kernels this library launched during sp2_run      */
   double backward_ms;             /* device time of the last sp2_backward              */
+  double tc_hw_flops;             /* tensor-core MMA flops issued in sp2_run (slice pairs,
+                                     zero padding of 128 x 128 super-tiles included)    */
 } sp2_stats;
 
 typedef struct sp2_ctx sp2_ctx;

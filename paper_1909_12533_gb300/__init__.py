@@ -57,7 +57,7 @@ class sp2_stats(ctypes.Structure):
                 ("p", c_int32 * MAX_ITER), ("alpha", c_double * MAX_ITER), ("tau", c_double * MAX_ITER),
                 ("e", c_double * MAX_ITER), ("t", c_double * MAX_ITER), ("nnzb_hist", c_int64 * MAX_ITER),
                 ("prec_hist", c_int32 * MAX_ITER), ("kernel_launches", c_int64),
-                ("backward_ms", c_double)]
+                ("backward_ms", c_double), ("tc_hw_flops", c_double)]
 
 
 # Entry points declared in include/sp2.h: (name, restype, argtypes)

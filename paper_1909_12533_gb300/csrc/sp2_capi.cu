@@ -664,6 +664,7 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
     S.squares = 0;
     S.tile_triplets = 0;
     S.square_ms = 0.0;
+    S.tc_hw_flops = 0.0;
     S.have_estimates = 0;
     S.homo_est = S.lumo_est = NAN;
     for (int i = 0; i < SP2_MAX_ITER; ++i) {
@@ -672,8 +673,8 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       S.prec_hist[i] = -1;
     }
     const long long launches0 = g_launches;
-    c->ensure(c->errflag, 16);
-    c->ck(cudaMemsetAsync(c->errflag.p, 0, 16, c->st), "memset");
+    c->ensure(c->errflag, 32);
+    c->ck(cudaMemsetAsync(c->errflag.p, 0, 32, c->st), "memset");
     c->ck(cudaEventRecord(c->ev0, c->st), "event");
     // Algorithm 1: X_0 on F's pattern, then X~_0 = trunc(X_0, tau_0)
     const int64_t nF = c->F.nnzb;
@@ -737,10 +738,17 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       c->ck(launch_reduce_step(sa.part, nout, c->dsc.as<StepScalars>(), c->st), "reduce");
       c->ck(cudaMemcpyAsync(c->h_sc, c->dsc.p, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->st), "d2h");
       c->ck(cudaMemcpyAsync(c->h_cnt + 2, c->errflag.p, 4, cudaMemcpyDeviceToHost, c->st), "d2h");
+      c->ck(cudaMemcpyAsync(c->h_d2, c->errflag.as<char>() + 8, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
       c->sync();
       if (c->h_cnt[2] & 1) {
         c->last_error = "tensor-core square: a bounded wait timed out";
         throw Fail{SP2_ERR_TIMEOUT};
+      }
+      if (tc) {
+        const long long steps_total = *reinterpret_cast<long long*>(c->h_d2);
+        const int k = c->prm.slices;
+        const double pairs = (double)(k * (k + 1) / 2);
+        S.tc_hw_flops = (double)steps_total * pairs * 2.0 * 2.0 * 128.0 * 128.0 * 16.0;
       }
       float ms = 0.f;
       c->ck(cudaEventElapsedTime(&ms, c->evs0, c->evs1), "elapsed");

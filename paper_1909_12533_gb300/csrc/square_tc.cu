@@ -463,7 +463,11 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
-  if (threadIdx.x == 0 && (status[0] != 0 || !acc_ok) && a.err) atomicOr(a.err, 1);
+  if (threadIdx.x == 0 && a.err) {
+    if (status[0] != 0 || !acc_ok) atomicOr(a.err, 1);
+    // K steps issued (hardware MMA work = steps * pairs * 2 MMAs of 128x128x16)
+    atomicAdd(reinterpret_cast<unsigned long long*>(a.err + 2), (unsigned long long)nsteps);
+  }
 }
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
