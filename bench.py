@@ -40,6 +40,7 @@ WORKLOADS = {
     "water24k": dict(key=2, desc="water-like, 1000 molecules x 24 basis functions, N=24000, b=32, tau=1e-6, "
                                "Frobenius truncation, parameterless stop"),
     "water2k": dict(key="2s", desc="water-like, 101 molecules, N=2424, b=32, tau=1e-6"),
+    "water9k": dict(key="2m", desc="water-like, 400 molecules, N=9600, b=32, tau=1e-6"),
     "helix128k": dict(key=4, desc="helix-like chain, 2000 residues x 64, N=128000, tau=1e-6"),
     "dense512": dict(key=1, desc="dense N=512, tau=0, idempotency stop 1e-12"),
 }

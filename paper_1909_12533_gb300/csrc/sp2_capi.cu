@@ -455,7 +455,7 @@ void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool) {
   const int nsr = (c->nb + 3) / 4;
   c->ensure(c->sbits, (size_t)nsr * c->words * 4);
   c->ck(launch_super_bits(c->fp, c->nb, nsr, c->sbits.as<uint32_t>(), c->st), "super bits");
-  const int64_t npair = (int64_t)nsr * nsr;
+  const int64_t npair = super_order_size(nsr);
   c->ensure(c->sflag, (size_t)npair * 4);
   c->ensure(c->spos, (size_t)npair * 4);
   c->ensure(c->scantmp, scan_tmp_bytes(npair) + 4096);

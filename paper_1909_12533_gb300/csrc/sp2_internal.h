@@ -136,6 +136,7 @@ cudaError_t launch_make_slices(const TileSet& x, const double* pool, void* slice
                                cudaStream_t st);
 cudaError_t launch_zero_half(void* p, int64_t n, cudaStream_t st);
 cudaError_t launch_super_bits(const FullPattern& fp, int nb, int nsr, uint32_t* sb, cudaStream_t st);
+int64_t super_order_size(int nsr);   // length of the (padded) launch-order index space
 cudaError_t launch_super_flags(const uint32_t* obits, int nb, int words, int nsr, int32_t* flag, cudaStream_t st);
 cudaError_t launch_super_fill(const int32_t* flag, const int32_t* pos, int64_t n, int nsr, int32_t* list,
                               cudaStream_t st);

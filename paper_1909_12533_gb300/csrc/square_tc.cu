@@ -88,6 +88,17 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
       : "memory");
 }
 
+// Exact int64 value of an FP32 that holds an integer (|x| < 2^31): split at
+// 2^11 so both parts are below 2^22 and convert each with the FP32
+// magic-number add (1.5 * 2^23), which stays on the FP32/ALU pipes.
+__device__ __forceinline__ long long f32_int_to_ll(float x) {
+  const float hi = truncf(x * 0x1p-11f);          // exact: power-of-two scale, integer part
+  const float lo = fmaf(hi, -2048.0f, x);          // exact: |lo| < 2048
+  const int ih = __float_as_int(hi + 12582912.0f) - 0x4B400000;
+  const int il = __float_as_int(lo + 12582912.0f) - 0x4B400000;
+  return (long long)ih * 2048 + il;
+}
+
 // Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
 // core matrices of 8 rows x 16 bytes (128 contiguous bytes), LBO = byte stride
 // between core matrices along K, SBO = byte stride between 8-row groups.
@@ -192,13 +203,33 @@ __global__ void k_super_bits(const uint32_t* __restrict__ bits, int nb, int word
   sb[i] = m;
 }
 
-// flag of super-tile (R, C), R <= C: any output tile present
+// Launch order of the super-tiles: blocks of RB super-rows x CB super-columns,
+// row-major inside a block, blocks row-major.  CTAs that run at the same time
+// then share A panels (same super-row) and B panels (same super-column), so the
+// slices they stream are reused from L2 instead of each CTA pulling its own B
+// panel from HBM.
+constexpr int RB = 8, CB = 16;
+
+__host__ __device__ inline int64_t blocked_size(int nsr) {
+  const int64_t nbr = (nsr + RB - 1) / RB, nbc = (nsr + CB - 1) / CB;
+  return nbr * nbc * RB * CB;
+}
+
+__device__ inline void blocked_decode(int64_t i, int nsr, int& R, int& C) {
+  const int64_t nbc = (nsr + CB - 1) / CB;
+  const int64_t b = i / (RB * CB), w = i % (RB * CB);
+  R = (int)((b / nbc) * RB + w / CB);
+  C = (int)((b % nbc) * CB + w % CB);
+}
+
+// flag of the i-th super-tile (R, C) in launch order: R <= C and an output tile present
 __global__ void k_super_flags(const uint32_t* __restrict__ obits, int nb, int words, int nsr, int32_t* flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= (int64_t)nsr * nsr) return;
-  const int R = (int)(i / nsr), C = (int)(i % nsr);
+  if (i >= blocked_size(nsr)) return;
+  int R, C;
+  blocked_decode(i, nsr, R, C);
   int f = 0;
-  if (R <= C) {
+  if (R < nsr && C < nsr && R <= C) {
     for (int a = 0; a < 4 && !f; ++a) {
       const int row = 4 * R + a;
       if (row >= nb) break;
@@ -214,7 +245,9 @@ __global__ void k_super_fill(const int32_t* __restrict__ flag, const int32_t* __
                              int32_t* list) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= n || !flag[i]) return;
-  list[pos[i]] = (int32_t)i;  // R * nsr + C
+  int R, C;
+  blocked_decode(i, nsr, R, C);
+  list[pos[i]] = R * nsr + C;
 }
 
 // ------------------------------------------------------------------ main kernel
@@ -288,51 +321,67 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
   const uint32_t* sbI = a.sbits + (int64_t)R * a.words;
   const uint32_t* sbJ = a.sbits + (int64_t)C * a.words;
 
-  if (warp == 0 && lane == 0) {
-    // ---------------- producer
-    int base[8];
-    for (int q = 0; q < 8; ++q) {
-      const int row = (q < 4) ? I0 + q : J0 + (q - 4);
-      base[q] = (row < a.nb) ? a.frowptr[row] : 0;
-    }
+  if (warp == 0) {
+    // ---------------- producer warp: lane q < 8 owns operand tile q (A rows
+    // I0..I0+3, then B rows J0..J0+3); the 8 tile lookups and bulk copies of a
+    // K step run in parallel, lane 0 arms the stage barrier first.
+    const int q = lane;
+    const int row = (q < 4) ? I0 + q : J0 + (q - 4);
+    const bool own = q < 8 && row < a.nb;
+    // zero_slots[s] bit q: slot q of stage s currently holds zeros (absent
+    // tiles are zero-filled in shared memory once instead of being copied)
+    uint64_t zero_slots = 0;   // 8 bits per stage
+    int base = own ? a.frowptr[row] : 0;
     int step = 0;
     bool ok = true;
     for (int w = 0; w < a.words && ok; ++w) {
       uint32_t m = sbI[w] & sbJ[w];
-      uint32_t rowbits[8];
-      for (int q = 0; q < 8; ++q) {
-        const int row = (q < 4) ? I0 + q : J0 + (q - 4);
-        rowbits[q] = (row < a.nb) ? a.bits[(int64_t)row * a.words + w] : 0u;
-      }
-      while (m && ok) {
+      const uint32_t rb = own ? a.bits[(int64_t)row * a.words + w] : 0u;
+      while (m) {
         const int b = __ffs(m) - 1;
         m &= m - 1;
-        const uint32_t below = (1u << b) - 1u;
         const int s = step % Cfg::STAGES;
         const uint32_t par = ((step / Cfg::STAGES) & 1) ^ 1;
-        if (!mbar_wait(&empty[s], par)) { ok = false; status[0] = 1; break; }
-        unsigned char* dst = stage_base + s * Cfg::STAGE_BYTES;
-        mbar_expect_tx(&full[s], Cfg::STAGE_BYTES);
-        int amask = 0, bmask = 0;
-        for (int q = 0; q < 8; ++q) {
-          const void* src = a.zero;
-          if ((rowbits[q] >> b) & 1u) {
-            const uint32_t rf = a.fref[base[q] + __popc(rowbits[q] & below)];
-            const int64_t sl = (int64_t)(rf & ~REF_T);
-            const int orient = (rf & REF_T) ? 1 : 0;
-            src = a.slices + (sl * 2 + orient) * (int64_t)K * TE;
-            if (q < 4) amask |= 1 << q; else bmask |= 1 << (q - 4);
-          }
-          bulk_g2s(dst + q * Cfg::TILE_BLOCK, src, Cfg::TILE_BLOCK, &full[s]);
+        // the tile lookup does not depend on the stage: issue it before waiting
+        const bool present = (rb >> b) & 1u;
+        const void* src = nullptr;
+        if (present) {
+          const uint32_t rf = a.fref[base + __popc(rb & ((1u << b) - 1u))];
+          src = a.slices + ((int64_t)(rf & ~REF_T) * 2 + ((rf & REF_T) ? 1 : 0)) * (int64_t)K * TE;
         }
-        for (int x = 0; x < 4; ++x)
-          for (int y = 0; y < 4; ++y)
-            if (((amask >> x) & 1) && ((bmask >> y) & 1)) kcount[x * 4 + y] += 1;
+        const uint32_t pres = __ballot_sync(0xffffffffu, q < 8 && present) & 0xFFu;
+        int good = 1;
+        if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
+        good = __shfl_sync(0xffffffffu, good, 0);
+        if (!good) { ok = false; if (lane == 0) status[0] = 1; break; }
+        unsigned char* dst = stage_base + s * Cfg::STAGE_BYTES;
+        // zero-fill absent slots that do not hold zeros yet (whole warp, 16-byte stores)
+        uint32_t fill = ~pres & ~(uint32_t)(zero_slots >> (8 * s)) & 0xFFu;
+        if (fill) {
+          while (fill) {
+            const int slot = __ffs(fill) - 1;
+            fill &= fill - 1;
+            uint4* z4 = reinterpret_cast<uint4*>(dst + slot * Cfg::TILE_BLOCK);
+            for (int i = lane; i < Cfg::TILE_BLOCK / 16; i += 32) z4[i] = make_uint4(0u, 0u, 0u, 0u);
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+        }
+        zero_slots = (zero_slots & ~(0xFFull << (8 * s))) | ((uint64_t)(~pres & 0xFFu) << (8 * s));
+        if (lane == 0) mbar_expect_tx(&full[s], (uint32_t)__popc(pres) * Cfg::TILE_BLOCK);
+        __syncwarp();
+        if (q < 8 && present) bulk_g2s(dst + q * Cfg::TILE_BLOCK, src, Cfg::TILE_BLOCK, &full[s]);
+        if (lane == 0) {
+          const int amask = pres & 0xF, bmask = (pres >> 4) & 0xF;
+          for (int x = 0; x < 4; ++x)
+            for (int y = 0; y < 4; ++y)
+              if (((amask >> x) & 1) && ((bmask >> y) & 1)) kcount[x * 4 + y] += 1;
+        }
         ++step;
       }
-      for (int q = 0; q < 8; ++q) base[q] += __popc(rowbits[q]);
+      base += __popc(rb);
     }
-    status[1] = step;
+    if (lane == 0) status[1] = step;
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     int nsteps = 0;
@@ -407,8 +456,24 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
       }
     }
     double e2 = 0.0, trS = 0.0, trX = 0.0, n2 = 0.0;
+    // S = fx * UNIT with fx the exact fixed-point sum of the groups; the unit is
+    // folded into the coefficients: xn = c0 [diag] + c1 z + (c2 UNIT) fx,
+    // z - S = z - UNIT fx
+    const double c2u = a.c2 * Cfg::UNIT;
     for (int ch = 0; ch < 2; ++ch) {     // 16 columns per chunk
       const int col0 = b * 32 + ch * 16;
+      double zv[16];
+#pragma unroll
+      for (int i = 0; i < 16; ++i) zv[i] = 0.0;
+      if (oidx >= 0 && Zt) {
+        const double2* zp = reinterpret_cast<const double2*>(Zt + r * TB + ch * 16);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const double2 t2 = zp[i];
+          zv[2 * i] = t2.x;
+          zv[2 * i + 1] = t2.y;
+        }
+      }
       float g[K][16];
       if (nsteps > 0 && acc_ok) {
 #pragma unroll
@@ -422,6 +487,7 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
       }
       if (oidx < 0) continue;
       double* O = a.opool + (int64_t)oidx * TE;
+      double out[16];
 #pragma unroll
       for (int i = 0; i < 16; ++i) {
         const int c = ch * 16 + i;
@@ -429,17 +495,20 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
         const bool inside = gi < a.n && gj < a.n;
         long long fx = 0;
 #pragma unroll
-        for (int gg = 0; gg < K; ++gg) fx += __float2ll_rn(g[gg][i]) * (1ll << (11 * (K - 1 - gg)));
-        const double s = inside ? (double)fx * Cfg::UNIT : 0.0;
-        const double z = (inside && Zt) ? Zt[r * TB + c] : 0.0;
+        for (int gg = 0; gg < K; ++gg) fx += f32_int_to_ll(g[gg][i]) * (1ll << (11 * (K - 1 - gg)));
+        const double fxd = inside ? (double)fx : 0.0;
+        const double z = inside ? zv[i] : 0.0;
         const bool dg = inside && gi == gj;
-        const double xn = inside ? ((dg ? a.c0 : 0.0) + a.c1 * z) + a.c2 * s : 0.0;
-        O[r * TB + c] = xn;
-        const double d = z - s;
-        e2 += d * d;
-        n2 += xn * xn;
-        if (dg) { trS += s; trX += z; }
+        const double xn = inside ? fma(c2u, fxd, fma(a.c1, z, dg ? a.c0 : 0.0)) : 0.0;
+        out[i] = xn;
+        const double d = fma(fxd, -Cfg::UNIT, z);
+        e2 = fma(d, d, e2);
+        n2 = fma(xn, xn, n2);
+        if (dg) { trS += fxd * Cfg::UNIT; trX += z; }
       }
+      double2* op = reinterpret_cast<double2*>(O + r * TB + ch * 16);
+#pragma unroll
+      for (int i = 0; i < 8; ++i) op[i] = make_double2(out[2 * i], out[2 * i + 1]);
     }
     // warp reductions (the tile's 32 rows are this warp's 32 lanes)
     for (int o = 16; o > 0; o >>= 1) {
@@ -498,9 +567,11 @@ cudaError_t launch_super_bits(const FullPattern& fp, int nb, int nsr, uint32_t* 
   return cudaGetLastError();
 }
 
+int64_t super_order_size(int nsr) { return blocked_size(nsr); }
+
 cudaError_t launch_super_flags(const uint32_t* obits, int nb, int words, int nsr, int32_t* flag, cudaStream_t st) {
   ++g_launches;
-  k_super_flags<<<grid_for((int64_t)nsr * nsr, 256), 256, 0, st>>>(obits, nb, words, nsr, flag);
+  k_super_flags<<<grid_for(blocked_size(nsr), 256), 256, 0, st>>>(obits, nb, words, nsr, flag);
   return cudaGetLastError();
 }
 
