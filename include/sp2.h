@@ -104,7 +104,8 @@ typedef struct {
   int32_t mixed_from;      /* first iteration i whose square uses `precision` (earlier ones FP64); default 1 */
   int32_t mixed_until;     /* last iteration using `precision` (later ones FP64); 0 = no limit */
   int32_t ckpt_every;      /* adjoint checkpoint interval k (X~_i kept for i % k == 0); default 8 */
-  int32_t record_masks;    /* 1: keep per-iteration tile masks (needed by sp2_backward); default 1 */
+  int32_t record_masks;    /* 1: keep per-iteration tile masks and FP64 checkpoints (needed by
+                              sp2_backward; memory grows by one X~ per ckpt_every steps); default 0 */
 } sp2_params;
 
 typedef struct {

@@ -375,7 +375,9 @@ def _autograd_function():
         @staticmethod
         def forward(ctx, F_val, F_brow, F_bcol, n, nocc, homo_ub, lumo_lb, tau, params=None):
             F = _Tiles(int(n), F_brow, F_bcol, F_val.detach())
-            obj = SP2(F, nocc, homo_ub, lumo_lb, tau, **(params or {}))
+            prm = dict(params or {})
+            prm["record_masks"] = 1
+            obj = SP2(F, nocc, homo_ub, lumo_lb, tau, **prm)
             obj.run()
             if obj.code not in (SP2_OK, NOT_CONVERGED):
                 raise SP2Error(obj.code, "sp2_run")

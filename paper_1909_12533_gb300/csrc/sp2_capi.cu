@@ -260,6 +260,7 @@ struct sp2_ctx {
   std::vector<Rec> recs;
   std::vector<Buf> seg;
   Buf ident, fpB_bits, fpB_rowptr, fpB_col, fpB_ref, gpool[2], w_brow, w_bcol, w_rowptr, w_pool, dF;
+  Buf slicesB, sbitsB, amax;
   FullPattern fpB;
   double backward_ms = 0.0;
   StepScalars* h_sc = nullptr;
@@ -279,7 +280,8 @@ struct sp2_ctx {
                   &fp_col, &fp_ref, &counts, &p_e2, &p_trS, &p_trX, &p_n2, &p_kt, &keep, &scanbuf, &scantmp,
                   &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &slices, &zero16,
                   &sbits, &sflag, &spos, &slist, &errflag, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
-                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF};
+                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &slicesB, &sbitsB,
+                  &amax};
     for (Buf* b : all) bufs.push_back(b);
   }
 
@@ -442,25 +444,44 @@ bool use_tc(const sp2_ctx* c, int i) {
   return true;
 }
 
-// S = X~^2 on the output tiles with the tcgen05 FP16-slice kernel, fused epilogue.
-void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool) {
+// FP16 slices (scale: power of two applied before slicing) of the tiles of `x`
+// (values by slot in `pool`) into `slices`, plus the super-row bitmap of `fp`.
+void prepare_operand(sp2_ctx* c, const TileSet& x, const double* pool, int64_t slot_capacity, const FullPattern& fp,
+                     Buf& slices, Buf& sbits, double scale) {
+  const int k = c->prm.slices;
+  c->ensure(slices, (size_t)std::max<int64_t>(slot_capacity, 1) * 2 * slice_block_bytes(k));
+  c->ck(launch_make_slices(x, pool, slices.p, k, c->errflag.as<int32_t>(), scale, c->st), "make slices");
+  const int nsr = (c->nb + 3) / 4;
+  c->ensure(sbits, (size_t)nsr * c->words * 4);
+  c->ck(launch_super_bits(fp, c->nb, nsr, sbits.as<uint32_t>(), c->st), "super bits");
+}
+
+// Smallest power of two >= max |x| over the tiles of `x` (1 for an all-zero set).
+double pow2_scale(sp2_ctx* c, const TileSet& x, const double* pool) {
+  c->ensure(c->amax, 16);
+  c->ck(launch_absmax(x, pool, c->amax.as<unsigned long long>(), c->st), "absmax");
+  c->ck(cudaMemcpyAsync(c->h_d2, c->amax.p, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
+  c->sync();
+  const double m = c->h_d2[0];
+  if (!(m > 0.0) || !std::isfinite(m)) return 1.0;
+  int e = 0;
+  std::frexp(m, &e);            // m = f * 2^e, f in [0.5, 1)
+  return std::ldexp(1.0, e);    // 2^e > m
+}
+
+// Run the tcgen05 kernel on the output tiles given by the upper bitmap `obits`
+// (row offsets `orowptr`); L carries operands, coefficients and pools.
+void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowptr) {
   const int k = c->prm.slices;
   const size_t blk = slice_block_bytes(k);
-  const int64_t pool_tiles = (int64_t)(c->pool[c->cur].cap / ((size_t)TE * 8));
-  c->ensure(c->slices, (size_t)pool_tiles * 2 * blk);
   c->ensure(c->zero16, blk);
   c->ck(launch_zero_half(c->zero16.p, (int64_t)k * TE, c->st), "zero block");
-  c->ck(launch_make_slices(c->X, c->pool[c->cur].as<double>(), c->slices.p, k, c->errflag.as<int32_t>(), c->st),
-        "make slices");
   const int nsr = (c->nb + 3) / 4;
-  c->ensure(c->sbits, (size_t)nsr * c->words * 4);
-  c->ck(launch_super_bits(c->fp, c->nb, nsr, c->sbits.as<uint32_t>(), c->st), "super bits");
   const int64_t npair = super_order_size(nsr);
   c->ensure(c->sflag, (size_t)npair * 4);
   c->ensure(c->spos, (size_t)npair * 4);
   c->ensure(c->scantmp, scan_tmp_bytes(npair) + 4096);
-  c->ck(launch_super_flags(c->o_bits.as<uint32_t>(), c->nb, c->words, nsr, c->sflag.as<int32_t>(), c->st),
-        "super flags");
+  c->ck(launch_super_flags(obits, c->nb, c->words, nsr, c->sflag.as<int32_t>(), c->st), "super flags");
   c->ck(launch_scan_i32(c->sflag.as<int32_t>(), c->spos.as<int32_t>(), npair, c->dcnt.as<int32_t>(), c->scantmp.p,
                         c->st),
         "scan");
@@ -468,24 +489,37 @@ void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool) {
   c->ensure(c->slist, (size_t)std::max<int64_t>(nsuper, 1) * 4);
   c->ck(launch_super_fill(c->sflag.as<int32_t>(), c->spos.as<int32_t>(), npair, nsr, c->slist.as<int32_t>(), c->st),
         "super fill");
-  TcLaunch L;
-  L.X = &c->fp;
-  L.sbits = c->sbits.as<uint32_t>();
-  L.slices = c->slices.p;
   L.zero = c->zero16.p;
-  L.zpool = c->pool[c->cur].as<double>();
-  L.obits = c->o_bits.as<uint32_t>();
-  L.orowptr = c->o_rowptr.as<int32_t>();
+  L.obits = obits;
+  L.orowptr = orowptr;
   L.list = c->slist.as<int32_t>();
   L.nsuper = nsuper;
-  L.opool = outpool;
-  L.part = partials(c);
-  L.c0 = c0; L.c1 = c1; L.c2 = c2;
-  L.n = c->n; L.nb = c->nb; L.nsr = nsr; L.k = k;
+  L.n = c->n;
+  L.nb = c->nb;
+  L.nsr = nsr;
+  L.k = k;
   L.err = c->errflag.as<int32_t>();
   c->ck(cudaEventRecord(c->evs0, c->st), "event");
   c->ck(launch_square_tc(L, c->st), "square tc");
   c->ck(cudaEventRecord(c->evs1, c->st), "event");
+}
+
+// Forward: S = X~^2 on the product pattern (o_bits, upper only) with the fused epilogue.
+void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool) {
+  prepare_operand(c, c->X, c->pool[c->cur].as<double>(), c->X.nnzb, c->fp, c->slices, c->sbits, 1.0);
+  TcLaunch L{};
+  L.P = &c->fp; L.Q = &c->fp;
+  L.Psbits = c->sbits.as<uint32_t>(); L.Qsbits = L.Psbits;
+  L.Pslices = c->slices.p; L.Qslices = c->slices.p;
+  L.two_pass = false;
+  L.scale = 1.0;
+  L.Z = &c->fp;
+  L.zslot = c->X.slot;
+  L.zpool = c->pool[c->cur].as<double>();
+  L.opool = outpool;
+  L.part = partials(c);
+  L.c0 = c0; L.c1 = c1; L.c2 = c2;
+  run_tc(c, L, c->o_bits.as<uint32_t>(), c->o_rowptr.as<int32_t>());
 }
 
 int fill_stats_sched(sp2_ctx* c) {
@@ -528,7 +562,7 @@ int sp2_default_params(sp2_params* p) {
   p->mixed_from = 1;
   p->mixed_until = 0;
   p->ckpt_every = 8;
-  p->record_masks = 1;
+  p->record_masks = 0;
   return SP2_OK;
 }
 
@@ -692,8 +726,15 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
     int n_out = -1;
     bool converged = false;
     for (int i = 1; i <= sch.n_max + 1; ++i) {
-      // symbolic: both-triangle pattern of X~_{i-1}, product pattern (upper + diagonal)
-      build_full(c, c->X, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
+      const bool tc = use_tc(c, i);
+      // symbolic: both-triangle pattern of X~_{i-1}, product pattern (upper + diagonal);
+      // the tensor path addresses tiles by compact index (slices), the FP64 path by slot
+      TileSet Xc = c->X;
+      if (tc) {
+        ensure_ident(c, c->X.nnzb);
+        Xc.slot = c->ident.as<int32_t>();
+      }
+      build_full(c, Xc, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
       c->ensure(c->o_bits, (size_t)c->nb * c->words * 4);
       c->ensure(c->o_rowptr, (size_t)(c->nb + 1) * 4);
       c->ck(launch_product_bits(c->fp, c->fp, c->nb, c->o_bits.as<uint32_t>(), c->st), "product bits");
@@ -726,7 +767,6 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       sa.c0 = c0; sa.c1 = c1; sa.c2 = c2;
       sa.n = c->n; sa.nb = c->nb;
       sa.part = partials(c);
-      const bool tc = use_tc(c, i);
       if (tc) {
         square_tc(c, c0, c1, c2, sa.outpool);
       } else {
@@ -853,6 +893,8 @@ int sp2_backward(sp2_ctx* c, const sp2_bsr* W, sp2_bsr* dF) {
   if (n < 0 || (int)c->recs.size() < n + 1) return SP2_ERR_STATE;
   try {
     c->ck(cudaEventRecord(c->ev0, c->st), "event");
+    c->ensure(c->errflag, 32);
+    c->ck(cudaMemsetAsync(c->errflag.p, 0, 32, c->st), "memset");
     const Schedule& sch = c->sch;
     const int k = c->prm.ckpt_every;
     // W -> device, validated like F (diagonal tiles not required)
@@ -909,6 +951,26 @@ int sp2_backward(sp2_ctx* c, const sp2_bsr* W, sp2_bsr* dF) {
         ensure_partials(c, std::max<int64_t>(cur.nnzb, 1));
         double c0, c1, c2;
         coeffs(sch.p[j], sch.alpha[j], c0, c1, c2);
+        if (c->prm.precision == SP2_PREC_SPLIT16) {
+          // X~_j on its recorded tiles: P = Q = Z = X~_{j-1}
+          prepare_operand(c, prev, vals[j - 1 - cp], prev.nnzb, c->fpB, c->slicesB, c->sbitsB, 1.0);
+          c->ensure(c->o_bits, (size_t)c->nb * c->words * 4);
+          c->ck(launch_upper_bits(cur, c->nb, c->words, c->o_bits.as<uint32_t>(), c->st), "upper bits");
+          TcLaunch L{};
+          L.P = &c->fpB; L.Q = &c->fpB;
+          L.Psbits = c->sbitsB.as<uint32_t>(); L.Qsbits = L.Psbits;
+          L.Pslices = c->slicesB.p; L.Qslices = c->slicesB.p;
+          L.two_pass = false;
+          L.scale = 1.0;
+          L.Z = &c->fpB;
+          L.zpool = vals[j - 1 - cp];
+          L.opool = dst.as<double>();
+          L.part = partials(c);
+          L.c0 = c0; L.c1 = c1; L.c2 = c2;
+          run_tc(c, L, c->o_bits.as<uint32_t>(), cur.rowptr);
+          vals[j - cp] = dst.as<double>();
+          continue;
+        }
         SquareArgs sa;
         sa.A = &c->fpB; sa.apool = vals[j - 1 - cp];
         sa.B = &c->fpB; sa.bpool = vals[j - 1 - cp];
@@ -931,6 +993,28 @@ int sp2_backward(sp2_ctx* c, const sp2_bsr* W, sp2_bsr* dF) {
         ensure_partials(c, std::max<int64_t>(tp.nnzb, 1));
         double c0, c1, c2;
         coeffs(sch.p[i], sch.alpha[i], c0, c1, c2);
+        if (c->prm.precision == SP2_PREC_SPLIT16) {
+          // G_{i-1} on X~_{i-1}'s tiles: c1 G_i + c2 (G_i X~_{i-1} + X~_{i-1} G_i), two passes
+          const double sg = pow2_scale(c, tg, c->gpool[gcur].as<double>());
+          prepare_operand(c, tg, c->gpool[gcur].as<double>(), tg.nnzb, c->fp, c->slices, c->sbits, sg);
+          prepare_operand(c, tp, vals[i - 1 - cp], tp.nnzb, c->fpB, c->slicesB, c->sbitsB, 1.0);
+          c->ensure(c->o_bits, (size_t)c->nb * c->words * 4);
+          c->ck(launch_upper_bits(tp, c->nb, c->words, c->o_bits.as<uint32_t>(), c->st), "upper bits");
+          TcLaunch L{};
+          L.P = &c->fp; L.Q = &c->fpB;
+          L.Psbits = c->sbits.as<uint32_t>(); L.Qsbits = c->sbitsB.as<uint32_t>();
+          L.Pslices = c->slices.p; L.Qslices = c->slicesB.p;
+          L.two_pass = true;
+          L.scale = sg;
+          L.Z = &c->fp;
+          L.zpool = c->gpool[gcur].as<double>();
+          L.opool = c->gpool[nxt].as<double>();
+          L.part = partials(c);
+          L.c0 = 0.0; L.c1 = c1; L.c2 = c2;
+          run_tc(c, L, c->o_bits.as<uint32_t>(), tp.rowptr);
+          gcur = nxt;
+          continue;
+        }
         SquareArgs sa;
         sa.A = &c->fp; sa.apool = c->gpool[gcur].as<double>();
         sa.B = &c->fpB; sa.bpool = vals[i - 1 - cp];
@@ -951,7 +1035,12 @@ int sp2_backward(sp2_ctx* c, const sp2_bsr* W, sp2_bsr* dF) {
                        c->st),
           "dF");
     c->ck(cudaEventRecord(c->ev1, c->st), "event");
+    c->ck(cudaMemcpyAsync(c->h_cnt + 2, c->errflag.p, 4, cudaMemcpyDeviceToHost, c->st), "d2h");
     c->sync();
+    if (c->h_cnt[2] & 1) {
+      c->last_error = "tensor-core adjoint: a bounded wait timed out";
+      throw Fail{SP2_ERR_TIMEOUT};
+    }
     float ms = 0.f;
     c->ck(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "elapsed");
     c->backward_ms = ms;

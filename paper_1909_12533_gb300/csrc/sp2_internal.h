@@ -113,14 +113,23 @@ cudaError_t launch_place(const TileSet& src, const double* spool, const TileSet&
                          int sym_diag, cudaStream_t st);
 cudaError_t launch_iota(int32_t* p, int64_t n, cudaStream_t st);
 
-// square_tc.cu: tcgen05 FP16-slice product (see the file header)
+// square_tc.cu: tcgen05 FP16-slice product (see the file header).  The
+// operand patterns' refs are compact tile indices (slices are stored by tile
+// index); Z's values are found through zslot.
 struct TcLaunch {
-  const FullPattern* X;      // pattern of X~ (values: zpool, slices by slot)
-  const uint32_t* sbits;     // super-row bitmaps
-  const void* slices;        // FP16 slices [slot][2][k][1024]
+  const FullPattern* P;      // S = sum_K P_IK Q_KJ (+ Q_IK P_KJ when two_pass)
+  const FullPattern* Q;
+  const uint32_t* Psbits;    // super-row bitmaps of P and Q
+  const uint32_t* Qsbits;
+  const void* Pslices;       // FP16 slices [slot][2][k][1024] of P and Q
+  const void* Qslices;
+  bool two_pass;
+  double scale;              // product of the slice scales of P and Q (powers of two)
+  const FullPattern* Z;      // the c1 term's matrix (values: zpool)
+  const int32_t* zslot;      // value slot of each tile index of Z's pattern (nullptr: identity)
   const void* zero;          // k * 1024 FP16 zeros
   const double* zpool;
-  const uint32_t* obits;     // output pattern bitmap
+  const uint32_t* obits;     // output pattern bitmap (upper tiles only)
   const int32_t* orowptr;
   const int32_t* list;       // active super-tiles
   int64_t nsuper;
@@ -133,7 +142,9 @@ struct TcLaunch {
 };
 size_t slice_block_bytes(int k);
 cudaError_t launch_make_slices(const TileSet& x, const double* pool, void* slices, int k, int32_t* err,
-                               cudaStream_t st);
+                               double scale, cudaStream_t st);
+cudaError_t launch_absmax(const TileSet& x, const double* pool, unsigned long long* out, cudaStream_t st);
+cudaError_t launch_upper_bits(const TileSet& x, int nb, int words, uint32_t* bits, cudaStream_t st);
 cudaError_t launch_zero_half(void* p, int64_t n, cudaStream_t st);
 cudaError_t launch_super_bits(const FullPattern& fp, int nb, int nsr, uint32_t* sb, cudaStream_t st);
 int64_t super_order_size(int nsr);   // length of the (padded) launch-order index space

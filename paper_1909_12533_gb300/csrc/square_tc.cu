@@ -144,22 +144,22 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------------------ slicing
-// One CTA per stored tile: write both orientations (the tile and its
-// transpose) of the k slices in the interleaved K-major layout
+// One CTA per stored tile t (values at pool slot slot[t]): write both
+// orientations (the tile and its transpose) of the k slices, at index t, in
+// the interleaved K-major layout
 //   byte offset = g * (k * 512) + s * 512 + c * 128 + r * 16 + j * 2
 // for the element in row 8g + r, column 8c + j of slice s.
 template <int K>
 __global__ void __launch_bounds__(256) k_make_slices(const int32_t* __restrict__ slot, const double* __restrict__ pool,
-                                                      __half* slices, int32_t* err) {
+                                                      __half* slices, int32_t* err, double inv_scale) {
   const int64_t t = blockIdx.x;
-  const int64_t sl = slot[t];
-  const double* src = pool + sl * TE;
-  __half* dst0 = slices + (sl * 2 + 0) * (int64_t)K * (TE);
-  __half* dst1 = slices + (sl * 2 + 1) * (int64_t)K * (TE);
+  const double* src = pool + (int64_t)slot[t] * TE;
+  __half* dst0 = slices + (t * 2 + 0) * (int64_t)K * (TE);
+  __half* dst1 = slices + (t * 2 + 1) * (int64_t)K * (TE);
   constexpr int FIN = 11 * K - 1;                  // finest grid 2^-FIN
   for (int q = threadIdx.x; q < TE; q += blockDim.x) {
     const int r = q >> 5, c = q & 31;
-    double x = src[q];
+    double x = src[q] * inv_scale;
     if (!(fabs(x) < 2.0)) {
       if (err) atomicOr(err, 4);
       x = fmin(fmax(x, -1.999), 1.999);
@@ -251,20 +251,32 @@ __global__ void k_super_fill(const int32_t* __restrict__ flag, const int32_t* __
 }
 
 // ------------------------------------------------------------------ main kernel
-struct TcArgs {
-  const uint32_t* bits;     // X~ both-triangle bitmap [nb][words]
-  const int32_t* frowptr;   // X~ neighbour lists
+// One operand matrix of the product: both-triangle pattern, super-row bitmap
+// and FP16 slices (indexed by value slot).
+struct TcOperand {
+  const uint32_t* bits;
+  const int32_t* frowptr;
   const uint32_t* fref;
-  const uint32_t* sbits;    // super-row bitmaps [nsr][words]
-  const __half* slices;     // [slot][2][K][1024]
+  const uint32_t* sbits;
+  const __half* slices;
+};
+
+struct TcArgs {
+  TcOperand P, Q;           // S = sum_K P_IK Q_KJ  (+ Q_IK P_KJ when two_pass)
+  int two_pass;
+  const uint32_t* zbits;    // Z (the c1 term): pattern and FP64 values
+  const int32_t* zrowptr;
+  const uint32_t* zref;
+  const int32_t* zslot;     // value slot of Z's tile index (nullptr: identity)
+  const double* zpool;
   const __half* zero;       // K * 1024 zeros
-  const double* zpool;      // X~ FP64 values (slot-indexed)
-  const uint32_t* obits;    // output pattern bitmap
+  const uint32_t* obits;    // output pattern bitmap, upper tiles only
   const int32_t* orowptr;   // output tile row offsets
   const int32_t* list;      // active super-tiles, R * nsr + C
   double* opool;            // output tiles, slot = output index
   Partials part;
   double c0, c1, c2;
+  double scale;             // product of the operands' slice scales
   int64_t n;
   int nb, words, nsr;
   int32_t* err;
@@ -318,8 +330,6 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
 
-  const uint32_t* sbI = a.sbits + (int64_t)R * a.words;
-  const uint32_t* sbJ = a.sbits + (int64_t)C * a.words;
 
   if (warp == 0) {
     // ---------------- producer warp: lane q < 8 owns operand tile q (A rows
@@ -328,64 +338,74 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
     const int q = lane;
     const int row = (q < 4) ? I0 + q : J0 + (q - 4);
     const bool own = q < 8 && row < a.nb;
-    // zero_slots[s] bit q: slot q of stage s currently holds zeros (absent
-    // tiles are zero-filled in shared memory once instead of being copied)
-    uint64_t zero_slots = 0;   // 8 bits per stage
-    int base = own ? a.frowptr[row] : 0;
+    uint64_t zero_slots = 0;   // 8 bits per stage: slots that hold zeros
     int step = 0;
     bool ok = true;
-    for (int w = 0; w < a.words && ok; ++w) {
-      uint32_t m = sbI[w] & sbJ[w];
-      const uint32_t rb = own ? a.bits[(int64_t)row * a.words + w] : 0u;
-      while (m) {
-        const int b = __ffs(m) - 1;
-        m &= m - 1;
-        const int s = step % Cfg::STAGES;
-        const uint32_t par = ((step / Cfg::STAGES) & 1) ^ 1;
-        // the tile lookup does not depend on the stage: issue it before waiting
-        const bool present = (rb >> b) & 1u;
-        const void* src = nullptr;
-        if (present) {
-          const uint32_t rf = a.fref[base + __popc(rb & ((1u << b) - 1u))];
-          src = a.slices + ((int64_t)(rf & ~REF_T) * 2 + ((rf & REF_T) ? 1 : 0)) * (int64_t)K * TE;
-        }
-        const uint32_t pres = __ballot_sync(0xffffffffu, q < 8 && present) & 0xFFu;
-        int good = 1;
-        if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
-        good = __shfl_sync(0xffffffffu, good, 0);
-        if (!good) { ok = false; if (lane == 0) status[0] = 1; break; }
-        unsigned char* dst = stage_base + s * Cfg::STAGE_BYTES;
-        // zero-fill absent slots that do not hold zeros yet (whole warp, 16-byte stores)
-        uint32_t fill = ~pres & ~(uint32_t)(zero_slots >> (8 * s)) & 0xFFu;
-        if (fill) {
-          while (fill) {
-            const int slot = __ffs(fill) - 1;
-            fill &= fill - 1;
-            uint4* z4 = reinterpret_cast<uint4*>(dst + slot * Cfg::TILE_BLOCK);
-            for (int i = lane; i < Cfg::TILE_BLOCK / 16; i += 32) z4[i] = make_uint4(0u, 0u, 0u, 0u);
+    for (int pass = 0; pass < 1 + a.two_pass && ok; ++pass) {
+      // pass 0: A = P (rows I), B = Q (rows J); pass 1: A = Q, B = P
+      const TcOperand& opA = pass == 0 ? a.P : a.Q;
+      const TcOperand& opB = pass == 0 ? a.Q : a.P;
+      const TcOperand& mine = (q < 4) ? opA : opB;
+      const uint32_t* sA = opA.sbits + (int64_t)R * a.words;
+      const uint32_t* sB = opB.sbits + (int64_t)C * a.words;
+      int base = own ? mine.frowptr[row] : 0;
+      for (int w = 0; w < a.words && ok; ++w) {
+        uint32_t m = sA[w] & sB[w];
+        const uint32_t rb = own ? mine.bits[(int64_t)row * a.words + w] : 0u;
+        while (m) {
+          const int b = __ffs(m) - 1;
+          m &= m - 1;
+          const int s = step % Cfg::STAGES;
+          const uint32_t par = ((step / Cfg::STAGES) & 1) ^ 1;
+          // the tile lookup does not depend on the stage: issue it before waiting
+          const bool present = (rb >> b) & 1u;
+          const void* src = nullptr;
+          if (present) {
+            const uint32_t rf = mine.fref[base + __popc(rb & ((1u << b) - 1u))];
+            src = mine.slices + ((int64_t)(rf & ~REF_T) * 2 + ((rf & REF_T) ? 1 : 0)) * (int64_t)K * TE;
           }
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          const uint32_t pres = __ballot_sync(0xffffffffu, q < 8 && present) & 0xFFu;
+          int good = 1;
+          if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
+          good = __shfl_sync(0xffffffffu, good, 0);
+          if (!good) { ok = false; if (lane == 0) status[0] = 1; break; }
+          unsigned char* dst = stage_base + s * Cfg::STAGE_BYTES;
+          // zero-fill absent slots that do not hold zeros yet (whole warp, 16-byte stores)
+          uint32_t fill = ~pres & ~(uint32_t)(zero_slots >> (8 * s)) & 0xFFu;
+          if (fill) {
+            while (fill) {
+              const int slot = __ffs(fill) - 1;
+              fill &= fill - 1;
+              uint4* z4 = reinterpret_cast<uint4*>(dst + slot * Cfg::TILE_BLOCK);
+              for (int i = lane; i < Cfg::TILE_BLOCK / 16; i += 32) z4[i] = make_uint4(0u, 0u, 0u, 0u);
+            }
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            __syncwarp();
+          }
+          zero_slots = (zero_slots & ~(0xFFull << (8 * s))) | ((uint64_t)(~pres & 0xFFu) << (8 * s));
+          if (lane == 0) mbar_expect_tx(&full[s], (uint32_t)__popc(pres) * Cfg::TILE_BLOCK);
           __syncwarp();
+          if (q < 8 && present) bulk_g2s(dst + q * Cfg::TILE_BLOCK, src, Cfg::TILE_BLOCK, &full[s]);
+          if (lane == 0) {
+            const int amask = pres & 0xF, bmask = (pres >> 4) & 0xF;
+            for (int x = 0; x < 4; ++x)
+              for (int y = 0; y < 4; ++y)
+                if (((amask >> x) & 1) && ((bmask >> y) & 1)) kcount[x * 4 + y] += 1;
+          }
+          ++step;
         }
-        zero_slots = (zero_slots & ~(0xFFull << (8 * s))) | ((uint64_t)(~pres & 0xFFu) << (8 * s));
-        if (lane == 0) mbar_expect_tx(&full[s], (uint32_t)__popc(pres) * Cfg::TILE_BLOCK);
-        __syncwarp();
-        if (q < 8 && present) bulk_g2s(dst + q * Cfg::TILE_BLOCK, src, Cfg::TILE_BLOCK, &full[s]);
-        if (lane == 0) {
-          const int amask = pres & 0xF, bmask = (pres >> 4) & 0xF;
-          for (int x = 0; x < 4; ++x)
-            for (int y = 0; y < 4; ++y)
-              if (((amask >> x) & 1) && ((bmask >> y) & 1)) kcount[x * 4 + y] += 1;
-        }
-        ++step;
+        base += __popc(rb);
       }
-      base += __popc(rb);
     }
     if (lane == 0) status[1] = step;
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     int nsteps = 0;
-    for (int w = 0; w < a.words; ++w) nsteps += __popc(sbI[w] & sbJ[w]);
+    for (int w = 0; w < a.words; ++w)
+      nsteps += __popc(a.P.sbits[(int64_t)R * a.words + w] & a.Q.sbits[(int64_t)C * a.words + w]);
+    if (a.two_pass)
+      for (int w = 0; w < a.words; ++w)
+        nsteps += __popc(a.Q.sbits[(int64_t)R * a.words + w] & a.P.sbits[(int64_t)C * a.words + w]);
     bool ok = true;
     for (int step = 0; step < nsteps; ++step) {
       const int s = step % Cfg::STAGES;
@@ -443,23 +463,25 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
         oidx = pos + __popc(mo & ((1u << (Jb & 31)) - 1u));
       }
     }
-    // X~_IJ (absent -> 0)
+    // Z_IJ (X~_IJ in the forward step; absent -> 0)
     const double* Zt = nullptr;
     if (oidx >= 0) {
-      const uint32_t* bz = a.bits + (int64_t)Ia * a.words;
+      const uint32_t* bz = a.zbits + (int64_t)Ia * a.words;
       const uint32_t mz = bz[Jb >> 5];
       if ((mz >> (Jb & 31)) & 1u) {
-        int pos = a.frowptr[Ia];
+        int pos = a.zrowptr[Ia];
         for (int w = 0; w < (Jb >> 5); ++w) pos += __popc(bz[w]);
         pos += __popc(mz & ((1u << (Jb & 31)) - 1u));
-        Zt = a.zpool + (int64_t)(a.fref[pos] & ~REF_T) * TE;
+        const int64_t zi = (int64_t)(a.zref[pos] & ~REF_T);
+        Zt = a.zpool + (int64_t)(a.zslot ? a.zslot[zi] : zi) * TE;
       }
     }
     double e2 = 0.0, trS = 0.0, trX = 0.0, n2 = 0.0;
     // S = fx * UNIT with fx the exact fixed-point sum of the groups; the unit is
     // folded into the coefficients: xn = c0 [diag] + c1 z + (c2 UNIT) fx,
     // z - S = z - UNIT fx
-    const double c2u = a.c2 * Cfg::UNIT;
+    const double su = Cfg::UNIT * a.scale;
+    const double c2u = a.c2 * su;
     for (int ch = 0; ch < 2; ++ch) {     // 16 columns per chunk
       const int col0 = b * 32 + ch * 16;
       double zv[16];
@@ -501,10 +523,10 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
         const bool dg = inside && gi == gj;
         const double xn = inside ? fma(c2u, fxd, fma(a.c1, z, dg ? a.c0 : 0.0)) : 0.0;
         out[i] = xn;
-        const double d = fma(fxd, -Cfg::UNIT, z);
+        const double d = fma(fxd, -su, z);
         e2 = fma(d, d, e2);
         n2 = fma(xn, xn, n2);
-        if (dg) { trS += fxd * Cfg::UNIT; trX += z; }
+        if (dg) { trS += fxd * su; trX += z; }
       }
       double2* op = reinterpret_cast<double2*>(O + r * TB + ch * 16);
 #pragma unroll
@@ -546,12 +568,50 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 size_t slice_block_bytes(int k) { return (size_t)k * SLICE_BYTES; }
 
 cudaError_t launch_make_slices(const TileSet& x, const double* pool, void* slices, int k, int32_t* err,
-                               cudaStream_t st) {
+                               double scale, cudaStream_t st) {
   if (x.nnzb == 0) return cudaSuccess;
   __half* s = static_cast<__half*>(slices);
-  if (k == 2) { ++g_launches; k_make_slices<2><<<(unsigned)x.nnzb, 256, 0, st>>>(x.slot, pool, s, err); }
-  else if (k == 3) { ++g_launches; k_make_slices<3><<<(unsigned)x.nnzb, 256, 0, st>>>(x.slot, pool, s, err); }
-  else { ++g_launches; k_make_slices<4><<<(unsigned)x.nnzb, 256, 0, st>>>(x.slot, pool, s, err); }
+  const double inv = 1.0 / scale;   // scale is a power of two: exact
+  if (k == 2) { ++g_launches; k_make_slices<2><<<(unsigned)x.nnzb, 256, 0, st>>>(x.slot, pool, s, err, inv); }
+  else if (k == 3) { ++g_launches; k_make_slices<3><<<(unsigned)x.nnzb, 256, 0, st>>>(x.slot, pool, s, err, inv); }
+  else { ++g_launches; k_make_slices<4><<<(unsigned)x.nnzb, 256, 0, st>>>(x.slot, pool, s, err, inv); }
+  return cudaGetLastError();
+}
+
+// max |x| over the tiles of a set (for the power-of-two slice scale of G)
+__global__ void k_absmax(const int32_t* __restrict__ slot, const double* __restrict__ pool, int64_t nnzb,
+                         unsigned long long* out) {
+  double m = 0.0;
+  for (int64_t t = blockIdx.x; t < nnzb; t += gridDim.x) {
+    const double* x = pool + (int64_t)slot[t] * TE;
+    for (int q = threadIdx.x; q < TE; q += blockDim.x) m = fmax(m, fabs(x[q]));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, (unsigned long long)__double_as_longlong(m));
+}
+
+cudaError_t launch_absmax(const TileSet& x, const double* pool, unsigned long long* out, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(unsigned long long), st);
+  if (e != cudaSuccess || x.nnzb == 0) return e;
+  ++g_launches;
+  k_absmax<<<(unsigned)std::min<int64_t>(x.nnzb, 152 * 8), 256, 0, st>>>(x.slot, pool, x.nnzb, out);
+  return cudaGetLastError();
+}
+
+// upper-triangle bitmap of a tile set (bit J of row I for I <= J only)
+__global__ void k_upper_bits(const int32_t* __restrict__ brow, const int32_t* __restrict__ bcol, int64_t nnzb,
+                             uint32_t* bits, int words) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnzb) return;
+  const int i = brow[t], j = bcol[t];
+  atomicOr(&bits[(int64_t)i * words + (j >> 5)], 1u << (j & 31));
+}
+
+cudaError_t launch_upper_bits(const TileSet& x, int nb, int words, uint32_t* bits, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(bits, 0, (size_t)nb * words * 4, st);
+  if (e != cudaSuccess || x.nnzb == 0) return e;
+  ++g_launches;
+  k_upper_bits<<<grid_for(x.nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.nnzb, bits, words);
   return cudaGetLastError();
 }
 
@@ -585,11 +645,14 @@ cudaError_t launch_super_fill(const int32_t* flag, const int32_t* pos, int64_t n
 cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   if (L.nsuper == 0) return cudaSuccess;
   TcArgs a;
-  a.bits = L.X->bits; a.frowptr = L.X->rowptr; a.fref = L.X->ref;
-  a.sbits = L.sbits; a.slices = static_cast<const __half*>(L.slices); a.zero = static_cast<const __half*>(L.zero);
-  a.zpool = L.zpool; a.obits = L.obits; a.orowptr = L.orowptr; a.list = L.list; a.opool = L.opool;
-  a.part = L.part; a.c0 = L.c0; a.c1 = L.c1; a.c2 = L.c2; a.n = L.n; a.nb = L.nb; a.words = L.X->words;
-  a.nsr = L.nsr; a.err = L.err;
+  a.P = TcOperand{L.P->bits, L.P->rowptr, L.P->ref, L.Psbits, static_cast<const __half*>(L.Pslices)};
+  a.Q = TcOperand{L.Q->bits, L.Q->rowptr, L.Q->ref, L.Qsbits, static_cast<const __half*>(L.Qslices)};
+  a.two_pass = L.two_pass ? 1 : 0;
+  a.zbits = L.Z->bits; a.zrowptr = L.Z->rowptr; a.zref = L.Z->ref; a.zslot = L.zslot; a.zpool = L.zpool;
+  a.zero = static_cast<const __half*>(L.zero);
+  a.obits = L.obits; a.orowptr = L.orowptr; a.list = L.list; a.opool = L.opool;
+  a.part = L.part; a.c0 = L.c0; a.c1 = L.c1; a.c2 = L.c2; a.scale = L.scale; a.n = L.n; a.nb = L.nb;
+  a.words = L.P->words; a.nsr = L.nsr; a.err = L.err;
   cudaError_t e = cudaSuccess;
   switch (L.k) {
     case 2:

@@ -32,7 +32,7 @@ def test_binding_covers_header():
 def test_default_params_and_strerror():
     p = sp2.sp2_default_params()
     assert p.mode == 1 and p.stop == 0 and p.trunc == 0 and p.frobinf_part == 4096
-    assert p.n_max_cap == 100 and p.ckpt_every == 8 and p.slices == 4
+    assert p.n_max_cap == 100 and p.ckpt_every == 8 and p.slices == 4 and p.record_masks == 0
     assert sp2.sp2_strerror(0) == "ok"
     assert "bounds" in sp2.sp2_strerror(-2)
 

@@ -19,7 +19,7 @@ def _sym(rng, n):
 def _gpu_grad(Fb, nocc, hub, llb, tau, Wd, **kw):
     import paper_1909_12533_gb300 as sp2
     W = from_dense(Wd, keep_zero_tiles=True)
-    ctx = sp2.SP2(Fb, nocc, hub, llb, tau, **kw)
+    ctx = sp2.SP2(Fb, nocc, hub, llb, tau, record_masks=1, **kw)
     st = ctx.run()
     brow, bcol, val = ctx.backward(W)
     ctx.close()
@@ -107,7 +107,7 @@ def test_adjoint_truncated_helix_prefix_matches_oracle(ckpt):
     Wb = random_symmetric_on_pattern(Fb, seed=4)
     Wd = to_dense(Wb)
     import paper_1909_12533_gb300 as sp2
-    ctx = sp2.SP2(Fb, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], ckpt_every=ckpt)
+    ctx = sp2.SP2(Fb, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], ckpt_every=ckpt, record_masks=1)
     st = ctx.run()
     brow, bcol, val = ctx.backward(Wb)
     ctx.close()
@@ -136,6 +136,7 @@ def test_autograd_function():
     bc = torch.from_numpy(Fb.bcol).cuda()
     Fn = sp2.SP2Function
     Dv, Db, Dc = Fn.apply(Fv, br, bc, n, nocc, d["homo_ub"], d["lumo_lb"], 0.0, {"stop": "idempotency"})
+    # SP2Function records the masks itself
     # L = sum of stored D tiles weighted by a random tensor
     R = torch.randn(Dv.shape, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(1))
     L = (Dv * R).sum()
@@ -159,3 +160,51 @@ def test_autograd_function():
         fd = (loss(vp) - loss(vm)) / (2 * h)
         an = g[t, r_, c_] + (g[t, c_, r_] if (Fb.brow[t] == Fb.bcol[t] and r_ != c_) else 0.0)
         assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (t, r_, c_, fd, an)
+
+
+def test_adjoint_split16_matches_oracle_helix_prefix():
+    # tensor-core adjoint (G sliced with a power-of-two scale, two-pass G X + X G)
+    c = make_config("4s")
+    Fb = c["F"]
+    Wb = random_symmetric_on_pattern(Fb, seed=4)
+    import paper_1909_12533_gb300 as sp2
+    ctx = sp2.SP2(Fb, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], precision="split16", slices=4,
+                  record_masks=1)
+    st = ctx.run()
+    brow, bcol, val = ctx.backward(Wb)
+    bms = sp2.stats_dict(sp2.sp2_get_stats(ctx.ctx))["backward_ms"]
+    ctx.close()
+    dF = BlockSparse(n=Fb.n, brow=brow.cpu().numpy(), bcol=bcol.cpu().numpy(), val=val.cpu().numpy())
+    Fd = to_dense(Fb)
+    r = O.sp2(Fd, c["nocc"], c["homo_ub"], c["lumo_lb"], tau=c["tau"],
+              input_pattern=set(zip(Fb.brow.tolist(), Fb.bcol.tolist())))
+    mask = np.zeros_like(Fd)
+    for i, j in zip(Fb.brow.tolist(), Fb.bcol.tolist()):
+        mask[i * 32:(i + 1) * 32, j * 32:(j + 1) * 32] = 1
+        mask[j * 32:(j + 1) * 32, i * 32:(i + 1) * 32] = 1
+    G = O.adjoint_sp2(Fd, r, to_dense(Wb)) * mask
+    rel = np.linalg.norm(_dense_grad(dF) - G) / np.linalg.norm(G)
+    print(f"split16 adjoint rel err {rel:.2e}, backward {bms:.1f} ms")
+    assert st["n"] == r.n
+    assert rel <= 1e-6
+
+
+def test_adjoint_split16_central_finite_differences():
+    n, nocc = 64, 25
+    d = dense_gapped(n, nocc, (-1.5, -0.4), (0.4, 1.5), seed=78)
+    W = _sym(np.random.default_rng(7), n)
+    kw = dict(stop="idempotency", idem_tol=1e-11, precision="split16", slices=4)
+    dF, _ = _gpu_grad(from_dense(d["F"]), nocc, d["homo_ub"], d["lumo_lb"], 0.0, W, **kw)
+    G = _dense_grad(dF)
+    F = d["F"]
+    h = 1e-5
+    for (i, j) in [(0, 0), (5, 9), (40, 41), (63, 63)]:
+        Fp = F.copy(); Fm = F.copy()
+        Fp[i, j] += h; Fm[i, j] -= h
+        if i != j:
+            Fp[j, i] += h; Fm[j, i] -= h
+        Lp, _ = _loss_gpu(Fp, nocc, d["homo_ub"], d["lumo_lb"], 0.0, W, **kw)
+        Lm, _ = _loss_gpu(Fm, nocc, d["homo_ub"], d["lumo_lb"], 0.0, W, **kw)
+        fd = (Lp - Lm) / (2 * h)
+        an = G[i, j] + (G[j, i] if i != j else 0.0)
+        assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (i, j, fd, an)
