@@ -42,6 +42,8 @@ WORKLOADS = {
     "water2k": dict(key="2s", desc="water-like, 101 molecules, N=2424, b=32, tau=1e-6"),
     "water9k": dict(key="2m", desc="water-like, 400 molecules, N=9600, b=32, tau=1e-6"),
     "helix128k": dict(key=4, desc="helix-like chain, 2000 residues x 64, N=128000, tau=1e-6"),
+    "water192k": dict(key=3, desc="water-like, 8000 molecules x 24, N=192000, b=32, tau=1e-5"),
+    "dense16k": dict(key=5, desc="dense N=16384, gap 0.05, tau=0, idempotency stop 1e-12"),
     "dense512": dict(key=1, desc="dense N=512, tau=0, idempotency stop 1e-12"),
 }
 CPU_SAMPLE_KEY = "2s"
