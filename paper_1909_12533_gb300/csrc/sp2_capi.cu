@@ -247,7 +247,9 @@ struct sp2_ctx {
   // F (kept for the adjoint) and X~ (current iterate, values in pool[cur])
   TileSet F, X, out;
   Buf f_brow, f_bcol, f_slot, f_rowptr, f_pool;
-  Buf x_brow, x_bcol, x_slot, x_rowptr;
+  Buf x_brow, x_bcol, x_slot, x_rowptr;      // index set 0 of X~
+  Buf y_brow, y_bcol, y_slot, y_rowptr;      // index set 1 (the next X~ while the stop test is pending)
+  int xset = 0;
   Buf o_brow, o_bcol, o_slot, o_rowptr, o_bits;
   Buf pool[2];
   int cur = 0;
@@ -255,7 +257,7 @@ struct sp2_ctx {
   Buf fp_bits, fp_rowptr, fp_col, fp_ref, counts;
   Buf p_e2, p_trS, p_trX, p_n2, p_kt, keep, scanbuf, scantmp, twork, rowlo, rowhi;
   Buf dsc, dcnt, d2;
-  Buf slices, zero16, sbits, sflag, spos, slist, errflag;
+  Buf slices, zero16, sbits, sflag, spos, slist, errflag, scount;
   // adjoint
   std::vector<Rec> recs;
   std::vector<Buf> seg;
@@ -276,10 +278,11 @@ struct sp2_ctx {
 
   sp2_ctx() {
     Buf* all[] = {&f_brow, &f_bcol, &f_slot, &f_rowptr, &f_pool, &x_brow, &x_bcol, &x_slot, &x_rowptr,
+                  &y_brow, &y_bcol, &y_slot, &y_rowptr,
                   &o_brow, &o_bcol, &o_slot, &o_rowptr, &o_bits, &pool[0], &pool[1], &fp_bits, &fp_rowptr,
                   &fp_col, &fp_ref, &counts, &p_e2, &p_trS, &p_trX, &p_n2, &p_kt, &keep, &scanbuf, &scantmp,
                   &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &slices, &zero16,
-                  &sbits, &sflag, &spos, &slist, &errflag, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
+                  &sbits, &sflag, &spos, &slist, &errflag, &scount, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
                   &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &slicesB, &sbitsB,
                   &amax};
     for (Buf* b : all) bufs.push_back(b);
@@ -366,8 +369,9 @@ int32_t read_count(sp2_ctx* c, const int32_t* dev) {
 }
 
 // Truncate the tile set `in` (values indexed by slot, norms in n2[slot]) and
-// compact its index into the X buffers.
-void truncate_into_X(sp2_ctx* c, const TileSet& in, const double* n2, double tau) {
+// compact its index into index set `set`; the kept-tile count is left in dcnt[0]
+// (no host round trip).  Returns the target TileSet (nnzb not yet known).
+TileSet truncate_launch(sp2_ctx* c, const TileSet& in, const double* n2, double tau, int set) {
   const int64_t part_tiles = std::max<int64_t>(1, c->prm.frobinf_part / TB);
   // n2 may live in p_n2: only the flag buffers are (re)sized here
   c->ensure(c->keep, (size_t)std::max<int64_t>(in.nnzb, 1) * 4);
@@ -376,18 +380,35 @@ void truncate_into_X(sp2_ctx* c, const TileSet& in, const double* n2, double tau
   c->ck(launch_truncate(in, n2, c->nb, tau, c->prm.trunc, part_tiles, c->twork.p, c->keep.as<int32_t>(), c->st),
         "truncate");
   const size_t cap = (size_t)std::max<int64_t>(in.nnzb, 1) * 4;
-  c->ensure(c->x_brow, cap);
-  c->ensure(c->x_bcol, cap);
-  c->ensure(c->x_slot, cap);
-  c->ensure(c->x_rowptr, (size_t)(c->nb + 1) * 4);
+  Buf& br = set ? c->y_brow : c->x_brow;
+  Buf& bc = set ? c->y_bcol : c->x_bcol;
+  Buf& sl = set ? c->y_slot : c->x_slot;
+  Buf& rp = set ? c->y_rowptr : c->x_rowptr;
+  c->ensure(br, cap);
+  c->ensure(bc, cap);
+  c->ensure(sl, cap);
+  c->ensure(rp, (size_t)(c->nb + 1) * 4);
   c->ensure(c->dcnt, 16);
   c->ensure(c->scantmp, scan_tmp_bytes(in.nnzb) + 4096);
-  set_tiles(c->X, c->x_brow, c->x_bcol, c->x_slot, c->x_rowptr, 0);
-  c->ck(launch_compact(in, c->keep.as<int32_t>(), c->nb, c->X, c->dcnt.as<int32_t>(), c->scantmp.p,
+  TileSet t;
+  set_tiles(t, br, bc, sl, rp, 0);
+  c->ck(launch_compact(in, c->keep.as<int32_t>(), c->nb, t, c->dcnt.as<int32_t>(), c->scantmp.p,
                        c->scanbuf.as<int32_t>(), c->st),
         "compact");
-  c->X.nnzb = read_count(c, c->dcnt.as<int32_t>());
+  return t;
+}
+
+// Make `t` (with its host-side count) the current X~ and build its row offsets.
+void adopt_X(sp2_ctx* c, TileSet t, int64_t nnzb, int set) {
+  t.nnzb = nnzb;
+  c->X = t;
+  c->xset = set;
   c->ck(launch_rowptr_from_brow(c->X.brow, c->X.nnzb, c->nb, c->X.rowptr, c->st), "rowptr");
+}
+
+void truncate_into_X(sp2_ctx* c, const TileSet& in, const double* n2, double tau) {
+  TileSet t = truncate_launch(c, in, n2, tau, 0);
+  adopt_X(c, t, read_count(c, c->dcnt.as<int32_t>()), 0);
 }
 
 void free_recs(sp2_ctx* c) {
@@ -482,17 +503,26 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   c->ensure(c->spos, (size_t)npair * 4);
   c->ensure(c->scantmp, scan_tmp_bytes(npair) + 4096);
   c->ck(launch_super_flags(obits, c->nb, c->words, nsr, c->sflag.as<int32_t>(), c->st), "super flags");
-  c->ck(launch_scan_i32(c->sflag.as<int32_t>(), c->spos.as<int32_t>(), npair, c->dcnt.as<int32_t>(), c->scantmp.p,
-                        c->st),
+  c->ensure(c->scount, 16);
+  c->ck(launch_scan_i32(c->sflag.as<int32_t>(), c->spos.as<int32_t>(), npair, c->scount.as<int32_t>(),
+                        c->scantmp.p, c->st),
         "scan");
-  const int64_t nsuper = read_count(c, c->dcnt.as<int32_t>());
-  c->ensure(c->slist, (size_t)std::max<int64_t>(nsuper, 1) * 4);
+  // no host round trip: a persistent kernel with one CTA per SM reads the
+  // number of active super-tiles and takes them from a work counter
+  const int64_t ubound = (int64_t)nsr * (nsr + 1) / 2;
+  c->ensure(c->slist, (size_t)std::max<int64_t>(ubound, 1) * 4);
+  c->ck(cudaMemsetAsync(c->scount.as<int32_t>() + 1, 0, 4, c->st), "memset");
+  int sms = 0;
+  c->ck(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0), "attribute");
+  const int64_t nsuper = std::min<int64_t>(std::max(sms, 1), std::max<int64_t>(ubound, 1));
   c->ck(launch_super_fill(c->sflag.as<int32_t>(), c->spos.as<int32_t>(), npair, nsr, c->slist.as<int32_t>(), c->st),
         "super fill");
   L.zero = c->zero16.p;
   L.obits = obits;
   L.orowptr = orowptr;
   L.list = c->slist.as<int32_t>();
+  L.count = c->scount.as<int32_t>();
+  L.work = c->scount.as<int32_t>() + 1;
   L.nsuper = nsuper;
   L.n = c->n;
   L.nb = c->nb;
@@ -776,9 +806,16 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       }
       c->ensure(c->dsc, sizeof(StepScalars));
       c->ck(launch_reduce_step(sa.part, nout, c->dsc.as<StepScalars>(), c->st), "reduce");
+      // X~_i = trunc(X_i, tau_i) before the stop test on e_{i-1} is known (X_i's tiles
+      // live in pool[nxt] at slot = output index); X~_{i-1} keeps its own index set
+      const bool more = i <= sch.n_max;
+      TileSet next;
+      if (more) next = truncate_launch(c, c->out, c->p_n2.as<double>(), sch.tau[i], 1 - c->xset);
+      // one host round trip per step: scalars, error flags, kept-tile count
       c->ck(cudaMemcpyAsync(c->h_sc, c->dsc.p, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->st), "d2h");
       c->ck(cudaMemcpyAsync(c->h_cnt + 2, c->errflag.p, 4, cudaMemcpyDeviceToHost, c->st), "d2h");
       c->ck(cudaMemcpyAsync(c->h_d2, c->errflag.as<char>() + 8, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
+      if (more) c->ck(cudaMemcpyAsync(c->h_cnt, c->dcnt.p, 4, cudaMemcpyDeviceToHost, c->st), "d2h");
       c->sync();
       if (c->h_cnt[2] & 1) {
         c->last_error = "tensor-core square: a bounded wait timed out";
@@ -810,9 +847,8 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
         stop = ev[j] < c->prm.idem_tol;
       }
       if (stop) { n_out = j; converged = true; break; }
-      if (i == sch.n_max + 1) { n_out = j; break; }
-      // X~_i = trunc(X_i, tau_i); X_i's tiles live in pool[nxt] at slot = output index
-      truncate_into_X(c, c->out, c->p_n2.as<double>(), sch.tau[i]);
+      if (!more) { n_out = j; break; }
+      adopt_X(c, next, c->h_cnt[0], 1 - c->xset);
       c->cur = nxt;
       S.nnzb_hist[i] = c->X.nnzb;
       record(c, i);

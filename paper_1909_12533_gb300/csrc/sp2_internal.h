@@ -132,7 +132,9 @@ struct TcLaunch {
   const uint32_t* obits;     // output pattern bitmap (upper tiles only)
   const int32_t* orowptr;
   const int32_t* list;       // active super-tiles
-  int64_t nsuper;
+  const int32_t* count;      // their number on the device
+  int32_t* work;             // work counter of the persistent kernel (zeroed by the caller)
+  int64_t nsuper;            // grid size (one CTA per SM, capped by the upper bound)
   double* opool;
   Partials part;
   double c0, c1, c2;

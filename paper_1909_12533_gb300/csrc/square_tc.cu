@@ -152,10 +152,11 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 template <int K>
 __global__ void __launch_bounds__(256) k_make_slices(const int32_t* __restrict__ slot, const double* __restrict__ pool,
                                                       __half* slices, int32_t* err, double inv_scale) {
+  // both orientations are assembled in shared memory, then written out with
+  // coalesced 16-byte stores (2 * k * 2 KB per tile)
+  __shared__ __align__(16) __half sm[2][K * TE];
   const int64_t t = blockIdx.x;
   const double* src = pool + (int64_t)slot[t] * TE;
-  __half* dst0 = slices + (t * 2 + 0) * (int64_t)K * (TE);
-  __half* dst1 = slices + (t * 2 + 1) * (int64_t)K * (TE);
   constexpr int FIN = 11 * K - 1;                  // finest grid 2^-FIN
   for (int q = threadIdx.x; q < TE; q += blockDim.x) {
     const int r = q >> 5, c = q & 31;
@@ -177,12 +178,14 @@ __global__ void __launch_bounds__(256) k_make_slices(const int32_t* __restrict__
 #pragma unroll
     for (int s = 0; s < K; ++s) {
       const __half h = __int2half_rn(T[s]);
-      const int o0 = (r >> 3) * (K * 256) + s * 256 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7);
-      const int o1 = (c >> 3) * (K * 256) + s * 256 + (r >> 3) * 64 + (c & 7) * 8 + (r & 7);
-      dst0[o0] = h;
-      dst1[o1] = h;
+      sm[0][(r >> 3) * (K * 256) + s * 256 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7)] = h;
+      sm[1][(c >> 3) * (K * 256) + s * 256 + (r >> 3) * 64 + (c & 7) * 8 + (r & 7)] = h;
     }
   }
+  __syncthreads();
+  const uint4* s4 = reinterpret_cast<const uint4*>(&sm[0][0]);
+  uint4* d4 = reinterpret_cast<uint4*>(slices + t * 2 * (int64_t)K * TE);
+  for (int i = threadIdx.x; i < 2 * K * TE / 8; i += blockDim.x) d4[i] = s4[i];
 }
 
 __global__ void k_zero_half(__half* p, int64_t n) {
@@ -273,6 +276,8 @@ struct TcArgs {
   const uint32_t* obits;    // output pattern bitmap, upper tiles only
   const int32_t* orowptr;   // output tile row offsets
   const int32_t* list;      // active super-tiles, R * nsr + C
+  const int32_t* count;     // number of active super-tiles (device)
+  int32_t* work;            // work counter (zero at launch)
   double* opool;            // output tiles, slot = output index
   Partials part;
   double c0, c1, c2;
@@ -302,13 +307,9 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
   uint64_t* accb = empty + Cfg::STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
   int32_t* kcount = reinterpret_cast<int32_t*>(tmem_slot + 2);   // [16] triplets per tile
-  int32_t* status = kcount + 16;                                   // [0] timeout flag, [1] nsteps
+  int32_t* status = kcount + 16;                                   // [0] timeout, [1] steps, [2] tile index
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int st = a.list[blockIdx.x];
-  const int R = st / a.nsr, C = st % a.nsr;
-  const int I0 = 4 * R, J0 = 4 * C;
-
   if (threadIdx.x == 0) {
     for (int s = 0; s < Cfg::STAGES; ++s) {
       mbar_init(&full[s], 1);
@@ -317,9 +318,7 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
     mbar_init(accb, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     status[0] = 0;
-    status[1] = 0;
   }
-  if (threadIdx.x < 16) kcount[threadIdx.x] = 0;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
                  : "memory");
@@ -329,236 +328,258 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *tmem_slot;
+  const int total = *a.count;
 
+  // Persistent: every CTA takes super-tiles from the work counter until none are
+  // left.  Pipeline stages and barrier phases continue across tiles (step_base),
+  // TMEM is allocated once; the accumulator barrier flips once per tile.
+  int step_base = 0;        // steps issued by this CTA before the current tile
+  uint64_t zero_slots = 0;  // producer: 8 bits per stage, slots that hold zeros
+  bool alive = true;
+  for (uint32_t tile_iter = 0; alive; ++tile_iter) {
+    if (threadIdx.x == 0) status[2] = atomicAdd(a.work, 1);
+    if (threadIdx.x < 16) kcount[threadIdx.x] = 0;
+    __syncthreads();
+    const int idx = status[2];
+    if (idx >= total || status[0] != 0) break;
+    const int st = a.list[idx];
+    const int R = st / a.nsr, C = st % a.nsr;
+    const int I0 = 4 * R, J0 = 4 * C;
 
-  if (warp == 0) {
-    // ---------------- producer warp: lane q < 8 owns operand tile q (A rows
-    // I0..I0+3, then B rows J0..J0+3); the 8 tile lookups and bulk copies of a
-    // K step run in parallel, lane 0 arms the stage barrier first.
-    const int q = lane;
-    const int row = (q < 4) ? I0 + q : J0 + (q - 4);
-    const bool own = q < 8 && row < a.nb;
-    uint64_t zero_slots = 0;   // 8 bits per stage: slots that hold zeros
-    int step = 0;
-    bool ok = true;
-    for (int pass = 0; pass < 1 + a.two_pass && ok; ++pass) {
-      // pass 0: A = P (rows I), B = Q (rows J); pass 1: A = Q, B = P
-      const TcOperand& opA = pass == 0 ? a.P : a.Q;
-      const TcOperand& opB = pass == 0 ? a.Q : a.P;
-      const TcOperand& mine = (q < 4) ? opA : opB;
-      const uint32_t* sA = opA.sbits + (int64_t)R * a.words;
-      const uint32_t* sB = opB.sbits + (int64_t)C * a.words;
-      int base = own ? mine.frowptr[row] : 0;
-      for (int w = 0; w < a.words && ok; ++w) {
-        uint32_t m = sA[w] & sB[w];
-        const uint32_t rb = own ? mine.bits[(int64_t)row * a.words + w] : 0u;
-        while (m) {
-          const int b = __ffs(m) - 1;
-          m &= m - 1;
-          const int s = step % Cfg::STAGES;
-          const uint32_t par = ((step / Cfg::STAGES) & 1) ^ 1;
-          // the tile lookup does not depend on the stage: issue it before waiting
-          const bool present = (rb >> b) & 1u;
-          const void* src = nullptr;
-          if (present) {
-            const uint32_t rf = mine.fref[base + __popc(rb & ((1u << b) - 1u))];
-            src = mine.slices + ((int64_t)(rf & ~REF_T) * 2 + ((rf & REF_T) ? 1 : 0)) * (int64_t)K * TE;
-          }
-          const uint32_t pres = __ballot_sync(0xffffffffu, q < 8 && present) & 0xFFu;
-          int good = 1;
-          if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
-          good = __shfl_sync(0xffffffffu, good, 0);
-          if (!good) { ok = false; if (lane == 0) status[0] = 1; break; }
-          unsigned char* dst = stage_base + s * Cfg::STAGE_BYTES;
-          // zero-fill absent slots that do not hold zeros yet (whole warp, 16-byte stores)
-          uint32_t fill = ~pres & ~(uint32_t)(zero_slots >> (8 * s)) & 0xFFu;
-          if (fill) {
-            while (fill) {
-              const int slot = __ffs(fill) - 1;
-              fill &= fill - 1;
-              uint4* z4 = reinterpret_cast<uint4*>(dst + slot * Cfg::TILE_BLOCK);
-              for (int i = lane; i < Cfg::TILE_BLOCK / 16; i += 32) z4[i] = make_uint4(0u, 0u, 0u, 0u);
+    if (warp == 0) {
+      // ---------------- producer warp: lane q < 8 owns operand tile q (A rows
+      // I0..I0+3, then B rows J0..J0+3); the 8 tile lookups and bulk copies of a
+      // K step run in parallel, lane 0 arms the stage barrier first.
+      const int q = lane;
+      const int row = (q < 4) ? I0 + q : J0 + (q - 4);
+      const bool own = q < 8 && row < a.nb;
+      int step = step_base;
+      bool ok = true;
+      for (int pass = 0; pass < 1 + a.two_pass && ok; ++pass) {
+        // pass 0: A = P (rows I), B = Q (rows J); pass 1: A = Q, B = P
+        const TcOperand& opA = pass == 0 ? a.P : a.Q;
+        const TcOperand& opB = pass == 0 ? a.Q : a.P;
+        const TcOperand& mine = (q < 4) ? opA : opB;
+        const uint32_t* sA = opA.sbits + (int64_t)R * a.words;
+        const uint32_t* sB = opB.sbits + (int64_t)C * a.words;
+        int base = own ? mine.frowptr[row] : 0;
+        for (int w = 0; w < a.words && ok; ++w) {
+          uint32_t m = sA[w] & sB[w];
+          const uint32_t rb = own ? mine.bits[(int64_t)row * a.words + w] : 0u;
+          while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int s = step % Cfg::STAGES;
+            const uint32_t par = ((step / Cfg::STAGES) & 1) ^ 1;
+            // the tile lookup does not depend on the stage: issue it before waiting
+            const bool present = (rb >> b) & 1u;
+            const void* src = nullptr;
+            if (present) {
+              const uint32_t rf = mine.fref[base + __popc(rb & ((1u << b) - 1u))];
+              src = mine.slices + ((int64_t)(rf & ~REF_T) * 2 + ((rf & REF_T) ? 1 : 0)) * (int64_t)K * TE;
             }
-            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            const uint32_t pres = __ballot_sync(0xffffffffu, q < 8 && present) & 0xFFu;
+            int good = 1;
+            if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
+            good = __shfl_sync(0xffffffffu, good, 0);
+            if (!good) { ok = false; if (lane == 0) status[0] = 1; break; }
+            unsigned char* dst = stage_base + s * Cfg::STAGE_BYTES;
+            // zero-fill absent slots that do not hold zeros yet (whole warp, 16-byte stores)
+            uint32_t fill = ~pres & ~(uint32_t)(zero_slots >> (8 * s)) & 0xFFu;
+            if (fill) {
+              while (fill) {
+                const int slot = __ffs(fill) - 1;
+                fill &= fill - 1;
+                uint4* z4 = reinterpret_cast<uint4*>(dst + slot * Cfg::TILE_BLOCK);
+                for (int i = lane; i < Cfg::TILE_BLOCK / 16; i += 32) z4[i] = make_uint4(0u, 0u, 0u, 0u);
+              }
+              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+              __syncwarp();
+            }
+            zero_slots = (zero_slots & ~(0xFFull << (8 * s))) | ((uint64_t)(~pres & 0xFFu) << (8 * s));
+            if (lane == 0) mbar_expect_tx(&full[s], (uint32_t)__popc(pres) * Cfg::TILE_BLOCK);
             __syncwarp();
+            if (q < 8 && present) bulk_g2s(dst + q * Cfg::TILE_BLOCK, src, Cfg::TILE_BLOCK, &full[s]);
+            if (lane == 0) {
+              const int amask = pres & 0xF, bmask = (pres >> 4) & 0xF;
+              for (int x = 0; x < 4; ++x)
+                for (int y = 0; y < 4; ++y)
+                  if (((amask >> x) & 1) && ((bmask >> y) & 1)) kcount[x * 4 + y] += 1;
+            }
+            ++step;
           }
-          zero_slots = (zero_slots & ~(0xFFull << (8 * s))) | ((uint64_t)(~pres & 0xFFu) << (8 * s));
-          if (lane == 0) mbar_expect_tx(&full[s], (uint32_t)__popc(pres) * Cfg::TILE_BLOCK);
-          __syncwarp();
-          if (q < 8 && present) bulk_g2s(dst + q * Cfg::TILE_BLOCK, src, Cfg::TILE_BLOCK, &full[s]);
-          if (lane == 0) {
-            const int amask = pres & 0xF, bmask = (pres >> 4) & 0xF;
-            for (int x = 0; x < 4; ++x)
-              for (int y = 0; y < 4; ++y)
-                if (((amask >> x) & 1) && ((bmask >> y) & 1)) kcount[x * 4 + y] += 1;
-          }
-          ++step;
+          base += __popc(rb);
         }
-        base += __popc(rb);
       }
-    }
-    if (lane == 0) status[1] = step;
-  } else if (warp == 1 && lane == 0) {
-    // ---------------- MMA issuer
-    int nsteps = 0;
-    for (int w = 0; w < a.words; ++w)
-      nsteps += __popc(a.P.sbits[(int64_t)R * a.words + w] & a.Q.sbits[(int64_t)C * a.words + w]);
-    if (a.two_pass)
+      if (lane == 0) status[1] = step - step_base;
+    } else if (warp == 1 && lane == 0) {
+      // ---------------- MMA issuer
+      int nsteps = 0;
       for (int w = 0; w < a.words; ++w)
-        nsteps += __popc(a.Q.sbits[(int64_t)R * a.words + w] & a.P.sbits[(int64_t)C * a.words + w]);
-    bool ok = true;
-    for (int step = 0; step < nsteps; ++step) {
-      const int s = step % Cfg::STAGES;
-      const uint32_t par = (step / Cfg::STAGES) & 1;
-      if (!mbar_wait(&full[s], par)) { ok = false; status[0] = 1; break; }
-      tc_fence_after();
-      const uint32_t sA = smem_u32(stage_base + s * Cfg::STAGE_BYTES);
-      const uint32_t sB = sA + 4 * Cfg::TILE_BLOCK;
+        nsteps += __popc(a.P.sbits[(int64_t)R * a.words + w] & a.Q.sbits[(int64_t)C * a.words + w]);
+      if (a.two_pass)
+        for (int w = 0; w < a.words; ++w)
+          nsteps += __popc(a.Q.sbits[(int64_t)R * a.words + w] & a.P.sbits[(int64_t)C * a.words + w]);
+      bool ok = true;
+      for (int ls = 0; ls < nsteps; ++ls) {
+        const int step = step_base + ls;
+        const int s = step % Cfg::STAGES;
+        const uint32_t par = (step / Cfg::STAGES) & 1;
+        if (!mbar_wait(&full[s], par)) { ok = false; status[0] = 1; break; }
+        tc_fence_after();
+        const uint32_t sA = smem_u32(stage_base + s * Cfg::STAGE_BYTES);
+        const uint32_t sB = sA + 4 * Cfg::TILE_BLOCK;
 #pragma unroll
-      for (int ps = 0; ps < K; ++ps) {
+        for (int ps = 0; ps < K; ++ps) {
 #pragma unroll
-        for (int pt = 0; pt < K; ++pt) {
-          if (ps + pt > K - 1) continue;          // s + t <= k + 1 (1-based)
-          const uint32_t dcol = tmem + (uint32_t)((ps + pt) * ST);
+          for (int pt = 0; pt < K; ++pt) {
+            if (ps + pt > K - 1) continue;          // s + t <= k + 1 (1-based)
+            const uint32_t dcol = tmem + (uint32_t)((ps + pt) * ST);
 #pragma unroll
-          for (int kk = 0; kk < 2; ++kk) {
-            const uint64_t ad = make_desc(sA + ps * 512 + kk * 256, 128, K * 512);
-            const uint64_t bd = make_desc(sB + pt * 512 + kk * 256, 128, K * 512);
-            // the first MMA into each group accumulator (step 0, first K half,
-            // ps = 0, pt = group) overwrites it; all others accumulate
-            mma_f16(dcol, ad, bd, (step > 0 || kk > 0 || ps > 0) ? 1u : 0u);
+            for (int kk = 0; kk < 2; ++kk) {
+              const uint64_t ad = make_desc(sA + ps * 512 + kk * 256, 128, K * 512);
+              const uint64_t bd = make_desc(sB + pt * 512 + kk * 256, 128, K * 512);
+              // the first MMA into each group accumulator of a tile (its first
+              // step, first K half, ps = 0) overwrites it; all others accumulate
+              mma_f16(dcol, ad, bd, (ls > 0 || kk > 0 || ps > 0) ? 1u : 0u);
+            }
           }
         }
+        mma_commit(&empty[s]);
       }
-      mma_commit(&empty[s]);
+      if (!ok) status[0] = 1;
+      mma_commit(accb);   // arrives once every MMA issued above has completed
     }
-    if (!ok) status[0] = 1;
-    mma_commit(accb);   // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
-  __syncthreads();
+    __syncwarp();
+    __syncthreads();
 
-  // ---------------- epilogue (all 8 warps)
-  const int nsteps = status[1];
-  bool acc_ok = mbar_wait(accb, 0) && status[0] == 0;
-  tc_fence_after();
-  const int quarter = warp & 3;          // TMEM lanes 32*quarter .. +31
-  const int half = warp >> 2;            // columns 64*half .. +63
-  const int Ia = I0 + quarter;           // tile row of this thread
-  const int r = lane;                    // row inside the tile
-  const int64_t gi = (int64_t)Ia * TB + r;
-  // fixed-point weights of the groups: unit of group g (0-based) is 2^-(11 (g+2) - 2)
-  for (int hb = 0; hb < 2; ++hb) {       // two tiles per half: b = 2*half + hb
-    const int b = 2 * half + hb;
-    const int Jb = J0 + b;
-    const bool valid = Ia < a.nb && Jb < a.nb && Ia <= Jb;
-    // output tile index (if present in the product pattern)
-    int oidx = -1;
-    if (valid) {
-      const uint32_t* ob = a.obits + (int64_t)Ia * a.words;
-      const uint32_t mo = ob[Jb >> 5];
-      if ((mo >> (Jb & 31)) & 1u) {
-        int pos = a.orowptr[Ia];
-        for (int w = 0; w < (Jb >> 5); ++w) pos += __popc(ob[w]);
-        oidx = pos + __popc(mo & ((1u << (Jb & 31)) - 1u));
-      }
-    }
-    // Z_IJ (X~_IJ in the forward step; absent -> 0)
-    const double* Zt = nullptr;
-    if (oidx >= 0) {
-      const uint32_t* bz = a.zbits + (int64_t)Ia * a.words;
-      const uint32_t mz = bz[Jb >> 5];
-      if ((mz >> (Jb & 31)) & 1u) {
-        int pos = a.zrowptr[Ia];
-        for (int w = 0; w < (Jb >> 5); ++w) pos += __popc(bz[w]);
-        pos += __popc(mz & ((1u << (Jb & 31)) - 1u));
-        const int64_t zi = (int64_t)(a.zref[pos] & ~REF_T);
-        Zt = a.zpool + (int64_t)(a.zslot ? a.zslot[zi] : zi) * TE;
-      }
-    }
-    double e2 = 0.0, trS = 0.0, trX = 0.0, n2 = 0.0;
-    // S = fx * UNIT with fx the exact fixed-point sum of the groups; the unit is
-    // folded into the coefficients: xn = c0 [diag] + c1 z + (c2 UNIT) fx,
-    // z - S = z - UNIT fx
-    const double su = Cfg::UNIT * a.scale;
-    const double c2u = a.c2 * su;
-    for (int ch = 0; ch < 2; ++ch) {     // 16 columns per chunk
-      const int col0 = b * 32 + ch * 16;
-      double zv[16];
-#pragma unroll
-      for (int i = 0; i < 16; ++i) zv[i] = 0.0;
-      if (oidx >= 0 && Zt) {
-        const double2* zp = reinterpret_cast<const double2*>(Zt + r * TB + ch * 16);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const double2 t2 = zp[i];
-          zv[2 * i] = t2.x;
-          zv[2 * i + 1] = t2.y;
+    // ---------------- epilogue (all 8 warps)
+    const int nsteps = status[1];
+    step_base += nsteps;
+    // block-uniform outcome of the bounded wait (a late completion must not split the CTA)
+    const bool acc_ok = !__syncthreads_or(!mbar_wait(accb, tile_iter & 1u) || status[0] != 0);
+    if (!acc_ok) alive = false;
+    tc_fence_after();
+    const int quarter = warp & 3;          // TMEM lanes 32*quarter .. +31
+    const int half = warp >> 2;            // columns 64*half .. +63
+    const int Ia = I0 + quarter;           // tile row of this thread
+    const int r = lane;                    // row inside the tile
+    const int64_t gi = (int64_t)Ia * TB + r;
+    for (int hb = 0; hb < 2 && alive; ++hb) {   // two tiles per half: b = 2*half + hb
+      const int b = 2 * half + hb;
+      const int Jb = J0 + b;
+      const bool valid = Ia < a.nb && Jb < a.nb && Ia <= Jb;
+      // output tile index (if present in the output pattern)
+      int oidx = -1;
+      if (valid) {
+        const uint32_t* ob = a.obits + (int64_t)Ia * a.words;
+        const uint32_t mo = ob[Jb >> 5];
+        if ((mo >> (Jb & 31)) & 1u) {
+          int pos = a.orowptr[Ia];
+          for (int w = 0; w < (Jb >> 5); ++w) pos += __popc(ob[w]);
+          oidx = pos + __popc(mo & ((1u << (Jb & 31)) - 1u));
         }
       }
-      float g[K][16];
-      if (nsteps > 0 && acc_ok) {
-#pragma unroll
-        for (int gg = 0; gg < K; ++gg)
-          tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(gg * ST + col0), g[gg]);
-      } else {
-#pragma unroll
-        for (int gg = 0; gg < K; ++gg)
-#pragma unroll
-          for (int i = 0; i < 16; ++i) g[gg][i] = 0.0f;
+      // Z_IJ (X~_IJ in the forward step; absent -> 0)
+      const double* Zt = nullptr;
+      if (oidx >= 0) {
+        const uint32_t* bz = a.zbits + (int64_t)Ia * a.words;
+        const uint32_t mz = bz[Jb >> 5];
+        if ((mz >> (Jb & 31)) & 1u) {
+          int pos = a.zrowptr[Ia];
+          for (int w = 0; w < (Jb >> 5); ++w) pos += __popc(bz[w]);
+          pos += __popc(mz & ((1u << (Jb & 31)) - 1u));
+          const int64_t zi = (int64_t)(a.zref[pos] & ~REF_T);
+          Zt = a.zpool + (int64_t)(a.zslot ? a.zslot[zi] : zi) * TE;
+        }
       }
-      if (oidx < 0) continue;
-      double* O = a.opool + (int64_t)oidx * TE;
-      double out[16];
+      double e2 = 0.0, trS = 0.0, trX = 0.0, n2 = 0.0;
+      // S = fx * UNIT * scale with fx the exact fixed-point sum of the groups; the
+      // unit is folded into the coefficients: xn = c0 [diag] + c1 z + (c2 su) fx
+      const double su = Cfg::UNIT * a.scale;
+      const double c2u = a.c2 * su;
+      for (int ch = 0; ch < 2; ++ch) {     // 16 columns per chunk
+        const int col0 = b * 32 + ch * 16;
+        double zv[16];
 #pragma unroll
-      for (int i = 0; i < 16; ++i) {
-        const int c = ch * 16 + i;
-        const int64_t gj = (int64_t)Jb * TB + c;
-        const bool inside = gi < a.n && gj < a.n;
-        long long fx = 0;
+        for (int i = 0; i < 16; ++i) zv[i] = 0.0;
+        if (oidx >= 0 && Zt) {
+          const double2* zp = reinterpret_cast<const double2*>(Zt + r * TB + ch * 16);
 #pragma unroll
-        for (int gg = 0; gg < K; ++gg) fx += f32_int_to_ll(g[gg][i]) * (1ll << (11 * (K - 1 - gg)));
-        const double fxd = inside ? (double)fx : 0.0;
-        const double z = inside ? zv[i] : 0.0;
-        const bool dg = inside && gi == gj;
-        const double xn = inside ? fma(c2u, fxd, fma(a.c1, z, dg ? a.c0 : 0.0)) : 0.0;
-        out[i] = xn;
-        const double d = fma(fxd, -su, z);
-        e2 = fma(d, d, e2);
-        n2 = fma(xn, xn, n2);
-        if (dg) { trS += fxd * su; trX += z; }
+          for (int i = 0; i < 8; ++i) {
+            const double2 t2 = zp[i];
+            zv[2 * i] = t2.x;
+            zv[2 * i + 1] = t2.y;
+          }
+        }
+        float g[K][16];
+        if (nsteps > 0) {
+#pragma unroll
+          for (int gg = 0; gg < K; ++gg)
+            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(gg * ST + col0), g[gg]);
+        } else {
+#pragma unroll
+          for (int gg = 0; gg < K; ++gg)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) g[gg][i] = 0.0f;
+        }
+        if (oidx < 0) continue;
+        double* O = a.opool + (int64_t)oidx * TE;
+        double out[16];
+#pragma unroll
+        for (int i = 0; i < 16; ++i) {
+          const int c = ch * 16 + i;
+          const int64_t gj = (int64_t)Jb * TB + c;
+          const bool inside = gi < a.n && gj < a.n;
+          long long fx = 0;
+#pragma unroll
+          for (int gg = 0; gg < K; ++gg) fx += f32_int_to_ll(g[gg][i]) * (1ll << (11 * (K - 1 - gg)));
+          const double fxd = inside ? (double)fx : 0.0;
+          const double z = inside ? zv[i] : 0.0;
+          const bool dg = inside && gi == gj;
+          const double xn = inside ? fma(c2u, fxd, fma(a.c1, z, dg ? a.c0 : 0.0)) : 0.0;
+          out[i] = xn;
+          const double d = fma(fxd, -su, z);
+          e2 = fma(d, d, e2);
+          n2 = fma(xn, xn, n2);
+          if (dg) { trS += fxd * su; trX += z; }
+        }
+        double2* op = reinterpret_cast<double2*>(O + r * TB + ch * 16);
+#pragma unroll
+        for (int i = 0; i < 8; ++i) op[i] = make_double2(out[2 * i], out[2 * i + 1]);
       }
-      double2* op = reinterpret_cast<double2*>(O + r * TB + ch * 16);
-#pragma unroll
-      for (int i = 0; i < 8; ++i) op[i] = make_double2(out[2 * i], out[2 * i + 1]);
+      // warp reductions (the tile's 32 rows are this warp's 32 lanes)
+      for (int o = 16; o > 0; o >>= 1) {
+        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
+        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
+        trS += __shfl_xor_sync(0xffffffffu, trS, o);
+        trX += __shfl_xor_sync(0xffffffffu, trX, o);
+      }
+      if (lane == 0 && oidx >= 0) {
+        const bool diag = Ia == Jb;
+        a.part.e2[oidx] = (diag ? 1.0 : 2.0) * e2;
+        a.part.n2[oidx] = n2;
+        a.part.trS[oidx] = diag ? trS : 0.0;
+        a.part.trX[oidx] = diag ? trX : 0.0;
+        a.part.ktiles[oidx] = kcount[quarter * 4 + b];
+      }
     }
-    // warp reductions (the tile's 32 rows are this warp's 32 lanes)
-    for (int o = 16; o > 0; o >>= 1) {
-      e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-      n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-      trS += __shfl_xor_sync(0xffffffffu, trS, o);
-      trX += __shfl_xor_sync(0xffffffffu, trX, o);
+    if (threadIdx.x == 0 && a.err) {
+      if (!acc_ok) atomicOr(a.err, 1);
+      // K steps issued (hardware MMA work = steps * pairs * 2 MMAs of 128x128x16)
+      atomicAdd(reinterpret_cast<unsigned long long*>(a.err + 2), (unsigned long long)nsteps);
     }
-    if (lane == 0 && oidx >= 0) {
-      const bool diag = Ia == Jb;
-      a.part.e2[oidx] = (diag ? 1.0 : 2.0) * e2;
-      a.part.n2[oidx] = n2;
-      a.part.trS[oidx] = diag ? trS : 0.0;
-      a.part.trX[oidx] = diag ? trX : 0.0;
-      a.part.ktiles[oidx] = kcount[quarter * 4 + b];
-    }
+    // TMEM reads of this tile are complete before the next tile's MMAs start
+    tc_fence_before();
+    __syncthreads();
+    tc_fence_after();
   }
-  tc_fence_before();
   __syncthreads();
   if (warp == 1) {
     tc_fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem) : "memory");
   }
-  if (threadIdx.x == 0 && a.err) {
-    if (status[0] != 0 || !acc_ok) atomicOr(a.err, 1);
-    // K steps issued (hardware MMA work = steps * pairs * 2 MMAs of 128x128x16)
-    atomicAdd(reinterpret_cast<unsigned long long*>(a.err + 2), (unsigned long long)nsteps);
-  }
+  if (threadIdx.x == 0 && status[0] != 0 && a.err) atomicOr(a.err, 1);
 }
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
@@ -650,7 +671,8 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   a.two_pass = L.two_pass ? 1 : 0;
   a.zbits = L.Z->bits; a.zrowptr = L.Z->rowptr; a.zref = L.Z->ref; a.zslot = L.zslot; a.zpool = L.zpool;
   a.zero = static_cast<const __half*>(L.zero);
-  a.obits = L.obits; a.orowptr = L.orowptr; a.list = L.list; a.opool = L.opool;
+  a.obits = L.obits; a.orowptr = L.orowptr; a.list = L.list; a.count = L.count; a.work = L.work;
+  a.opool = L.opool;
   a.part = L.part; a.c0 = L.c0; a.c1 = L.c1; a.c2 = L.c2; a.scale = L.scale; a.n = L.n; a.nb = L.nb;
   a.words = L.P->words; a.nsr = L.nsr; a.err = L.err;
   cudaError_t e = cudaSuccess;
