@@ -225,6 +225,12 @@ struct Fail {
   int code;
 };
 
+// Device buffers of one tensor-core operand: super-row bitmaps, per-word
+// record counts and offsets, record index words, headers and slices.
+struct OpBufs {
+  Buf sbits, cnt, spos, index, head, data;
+};
+
 // Per-iteration record for the adjoint: the kept tiles of X~_j and, every
 // ckpt_every steps, their FP64 values (contiguous, index order).
 struct Rec {
@@ -257,12 +263,13 @@ struct sp2_ctx {
   Buf fp_bits, fp_rowptr, fp_col, fp_ref, counts;
   Buf p_e2, p_trS, p_trX, p_n2, p_kt, keep, scanbuf, scantmp, twork, rowlo, rowhi;
   Buf dsc, dcnt, d2;
-  Buf slices, zero16, sbits, sflag, spos, slist, errflag, scount;
+  OpBufs opx, opy;   // tensor-core operands (the adjoint uses both)
+  Buf sflag, spos, slist, errflag, scount;
   // adjoint
   std::vector<Rec> recs;
   std::vector<Buf> seg;
   Buf ident, fpB_bits, fpB_rowptr, fpB_col, fpB_ref, gpool[2], w_brow, w_bcol, w_rowptr, w_pool, dF;
-  Buf slicesB, sbitsB, amax;
+  Buf amax;
   FullPattern fpB;
   double backward_ms = 0.0;
   StepScalars* h_sc = nullptr;
@@ -281,10 +288,10 @@ struct sp2_ctx {
                   &y_brow, &y_bcol, &y_slot, &y_rowptr,
                   &o_brow, &o_bcol, &o_slot, &o_rowptr, &o_bits, &pool[0], &pool[1], &fp_bits, &fp_rowptr,
                   &fp_col, &fp_ref, &counts, &p_e2, &p_trS, &p_trX, &p_n2, &p_kt, &keep, &scanbuf, &scantmp,
-                  &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &slices, &zero16,
-                  &sbits, &sflag, &spos, &slist, &errflag, &scount, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
-                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &slicesB, &sbitsB,
-                  &amax};
+                  &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &opx.sbits,
+                  &opx.cnt, &opx.spos, &opx.index, &opx.head, &opx.data, &opy.sbits, &opy.cnt, &opy.spos,
+                  &opy.index, &opy.head, &opy.data, &sflag, &spos, &slist, &errflag, &scount, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
+                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax};
     for (Buf* b : all) bufs.push_back(b);
   }
 
@@ -467,14 +474,44 @@ bool use_tc(const sp2_ctx* c, int i) {
 
 // FP16 slices (scale: power of two applied before slicing) of the tiles of `x`
 // (values by slot in `pool`) into `slices`, plus the super-row bitmap of `fp`.
-void prepare_operand(sp2_ctx* c, const TileSet& x, const double* pool, int64_t slot_capacity, const FullPattern& fp,
-                     Buf& slices, Buf& sbits, double scale) {
+// Panel records of the tiles of `x` (values at pool slot x.slot[t] of tile
+// index t) on its both-triangle pattern `fp`: super-row bitmaps, record
+// offsets, record index words, then the FP16 slices and header of every
+// record.  Reads the number of records back (one host round trip).
+TcOp prepare_operand(sp2_ctx* c, const TileSet& x, const double* pool, const FullPattern& fp, OpBufs& ob,
+                     double scale) {
   const int k = c->prm.slices;
-  c->ensure(slices, (size_t)std::max<int64_t>(slot_capacity, 1) * 2 * slice_block_bytes(k));
-  c->ck(launch_make_slices(x, pool, slices.p, k, c->errflag.as<int32_t>(), scale, c->st), "make slices");
   const int nsr = (c->nb + 3) / 4;
-  c->ensure(sbits, (size_t)nsr * c->words * 4);
-  c->ck(launch_super_bits(fp, c->nb, nsr, sbits.as<uint32_t>(), c->st), "super bits");
+  const int64_t nw = (int64_t)nsr * c->words;
+  c->ensure(ob.sbits, (size_t)nw * 4);
+  c->ck(launch_super_bits(fp, c->nb, nsr, ob.sbits.as<uint32_t>(), c->st), "super bits");
+  c->ensure(ob.cnt, (size_t)nw * 4);
+  c->ensure(ob.spos, (size_t)(nw + 1) * 4);
+  c->ensure(c->scantmp, scan_tmp_bytes(nw) + 4096);
+  c->ck(launch_popc_words(ob.sbits.as<uint32_t>(), nw, ob.cnt.as<int32_t>(), c->st), "popc");
+  c->ck(launch_scan_i32(ob.cnt.as<int32_t>(), ob.spos.as<int32_t>(), nw, ob.spos.as<int32_t>() + nw, c->scantmp.p,
+                        c->st),
+        "scan");
+  const int64_t nrec = read_count(c, ob.spos.as<int32_t>() + nw);
+  const size_t nr = (size_t)std::max<int64_t>(nrec, 1);
+  c->ensure(ob.index, nr * 16);
+  c->ensure(ob.head, nr);
+  c->ensure(ob.data, nr * panel_record_bytes(k));
+  if (nrec > 0) {
+    c->ck(cudaMemsetAsync(ob.index.p, 0xFF, (size_t)nrec * 16, c->st), "memset");
+    c->ck(launch_panel_fill(fp, c->nb, ob.sbits.as<uint32_t>(), ob.spos.as<int32_t>(), ob.index.as<uint32_t>(),
+                            c->st),
+          "record index");
+    c->ck(launch_panel_slices(ob.index.as<uint32_t>(), nrec, x.slot, pool, ob.data.p, ob.head.as<uint8_t>(), k,
+                              c->errflag.as<int32_t>(), scale, c->st),
+          "record slices");
+  }
+  TcOp op;
+  op.sbits = ob.sbits.as<uint32_t>();
+  op.spos = ob.spos.as<int32_t>();
+  op.head = ob.head.as<uint8_t>();
+  op.data = ob.data.p;
+  return op;
 }
 
 // Smallest power of two >= max |x| over the tiles of `x` (1 for an all-zero set).
@@ -494,9 +531,6 @@ double pow2_scale(sp2_ctx* c, const TileSet& x, const double* pool) {
 // (row offsets `orowptr`); L carries operands, coefficients and pools.
 void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowptr) {
   const int k = c->prm.slices;
-  const size_t blk = slice_block_bytes(k);
-  c->ensure(c->zero16, blk);
-  c->ck(launch_zero_half(c->zero16.p, (int64_t)k * TE, c->st), "zero block");
   const int nsr = (c->nb + 3) / 4;
   const int64_t npair = super_order_size(nsr);
   c->ensure(c->sflag, (size_t)npair * 4);
@@ -517,7 +551,6 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   const int64_t nsuper = std::min<int64_t>(std::max(sms, 1), std::max<int64_t>(ubound, 1));
   c->ck(launch_super_fill(c->sflag.as<int32_t>(), c->spos.as<int32_t>(), npair, nsr, c->slist.as<int32_t>(), c->st),
         "super fill");
-  L.zero = c->zero16.p;
   L.obits = obits;
   L.orowptr = orowptr;
   L.list = c->slist.as<int32_t>();
@@ -528,6 +561,7 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   L.nb = c->nb;
   L.nsr = nsr;
   L.k = k;
+  L.words = c->words;
   L.err = c->errflag.as<int32_t>();
   c->ck(cudaEventRecord(c->evs0, c->st), "event");
   c->ck(launch_square_tc(L, c->st), "square tc");
@@ -536,11 +570,9 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
 
 // Forward: S = X~^2 on the product pattern (o_bits, upper only) with the fused epilogue.
 void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool) {
-  prepare_operand(c, c->X, c->pool[c->cur].as<double>(), c->X.nnzb, c->fp, c->slices, c->sbits, 1.0);
   TcLaunch L{};
-  L.P = &c->fp; L.Q = &c->fp;
-  L.Psbits = c->sbits.as<uint32_t>(); L.Qsbits = L.Psbits;
-  L.Pslices = c->slices.p; L.Qslices = c->slices.p;
+  L.P = prepare_operand(c, c->X, c->pool[c->cur].as<double>(), c->fp, c->opx, 1.0);
+  L.Q = L.P;
   L.two_pass = false;
   L.scale = 1.0;
   L.Z = &c->fp;
@@ -822,10 +854,9 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
         throw Fail{SP2_ERR_TIMEOUT};
       }
       if (tc) {
-        const long long steps_total = *reinterpret_cast<long long*>(c->h_d2);
-        const int k = c->prm.slices;
-        const double pairs = (double)(k * (k + 1) / 2);
-        S.tc_hw_flops = (double)steps_total * pairs * 2.0 * 2.0 * 128.0 * 128.0 * 16.0;
+        // slice-pair products issued, each two 128 x 128 x 16 MMAs
+        const long long products = *reinterpret_cast<long long*>(c->h_d2);
+        S.tc_hw_flops = (double)products * 2.0 * 128.0 * 128.0 * 32.0;
       }
       float ms = 0.f;
       c->ck(cudaEventElapsedTime(&ms, c->evs0, c->evs1), "elapsed");
@@ -989,13 +1020,11 @@ int sp2_backward(sp2_ctx* c, const sp2_bsr* W, sp2_bsr* dF) {
         coeffs(sch.p[j], sch.alpha[j], c0, c1, c2);
         if (c->prm.precision == SP2_PREC_SPLIT16) {
           // X~_j on its recorded tiles: P = Q = Z = X~_{j-1}
-          prepare_operand(c, prev, vals[j - 1 - cp], prev.nnzb, c->fpB, c->slicesB, c->sbitsB, 1.0);
+          TcLaunch L{};
+          L.P = prepare_operand(c, prev, vals[j - 1 - cp], c->fpB, c->opy, 1.0);
+          L.Q = L.P;
           c->ensure(c->o_bits, (size_t)c->nb * c->words * 4);
           c->ck(launch_upper_bits(cur, c->nb, c->words, c->o_bits.as<uint32_t>(), c->st), "upper bits");
-          TcLaunch L{};
-          L.P = &c->fpB; L.Q = &c->fpB;
-          L.Psbits = c->sbitsB.as<uint32_t>(); L.Qsbits = L.Psbits;
-          L.Pslices = c->slicesB.p; L.Qslices = c->slicesB.p;
           L.two_pass = false;
           L.scale = 1.0;
           L.Z = &c->fpB;
@@ -1032,14 +1061,11 @@ int sp2_backward(sp2_ctx* c, const sp2_bsr* W, sp2_bsr* dF) {
         if (c->prm.precision == SP2_PREC_SPLIT16) {
           // G_{i-1} on X~_{i-1}'s tiles: c1 G_i + c2 (G_i X~_{i-1} + X~_{i-1} G_i), two passes
           const double sg = pow2_scale(c, tg, c->gpool[gcur].as<double>());
-          prepare_operand(c, tg, c->gpool[gcur].as<double>(), tg.nnzb, c->fp, c->slices, c->sbits, sg);
-          prepare_operand(c, tp, vals[i - 1 - cp], tp.nnzb, c->fpB, c->slicesB, c->sbitsB, 1.0);
+          TcLaunch L{};
+          L.P = prepare_operand(c, tg, c->gpool[gcur].as<double>(), c->fp, c->opx, sg);
+          L.Q = prepare_operand(c, tp, vals[i - 1 - cp], c->fpB, c->opy, 1.0);
           c->ensure(c->o_bits, (size_t)c->nb * c->words * 4);
           c->ck(launch_upper_bits(tp, c->nb, c->words, c->o_bits.as<uint32_t>(), c->st), "upper bits");
-          TcLaunch L{};
-          L.P = &c->fp; L.Q = &c->fpB;
-          L.Psbits = c->sbits.as<uint32_t>(); L.Qsbits = c->sbitsB.as<uint32_t>();
-          L.Pslices = c->slices.p; L.Qslices = c->slicesB.p;
           L.two_pass = true;
           L.scale = sg;
           L.Z = &c->fp;

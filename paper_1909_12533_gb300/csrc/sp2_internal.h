@@ -113,21 +113,23 @@ cudaError_t launch_place(const TileSet& src, const double* spool, const TileSet&
                          int sym_diag, cudaStream_t st);
 cudaError_t launch_iota(int32_t* p, int64_t n, cudaStream_t st);
 
-// square_tc.cu: tcgen05 FP16-slice product (see the file header).  The
-// operand patterns' refs are compact tile indices (slices are stored by tile
-// index); Z's values are found through zslot.
+// square_tc.cu: tcgen05 FP16-slice product (see the file header).  An
+// operand is stored as panel records: for each super-row R (tile rows
+// 4R..4R+3) and K tile present in its super-row bitmap, a header byte and the
+// k FP16 slices of the 4 tiles (see k_panel_slices); Z's values are found
+// through zslot.
+struct TcOp {
+  const uint32_t* sbits = nullptr;   // super-row bitmaps [nsr][words]
+  const int32_t* spos = nullptr;     // index of the first record of each (R, word) [nsr][words]
+  const uint8_t* head = nullptr;     // record headers
+  const void* data = nullptr;        // record slices, k * 8 KB each
+};
 struct TcLaunch {
-  const FullPattern* P;      // S = sum_K P_IK Q_KJ (+ Q_IK P_KJ when two_pass)
-  const FullPattern* Q;
-  const uint32_t* Psbits;    // super-row bitmaps of P and Q
-  const uint32_t* Qsbits;
-  const void* Pslices;       // FP16 slices [slot][2][k][1024] of P and Q
-  const void* Qslices;
+  TcOp P, Q;                 // S = sum_K P_IK Q_KJ (+ Q_IK P_KJ when two_pass)
   bool two_pass;
   double scale;              // product of the slice scales of P and Q (powers of two)
   const FullPattern* Z;      // the c1 term's matrix (values: zpool)
   const int32_t* zslot;      // value slot of each tile index of Z's pattern (nullptr: identity)
-  const void* zero;          // k * 1024 FP16 zeros
   const double* zpool;
   const uint32_t* obits;     // output pattern bitmap (upper tiles only)
   const int32_t* orowptr;
@@ -139,15 +141,17 @@ struct TcLaunch {
   Partials part;
   double c0, c1, c2;
   int64_t n;
-  int nb, nsr, k;
+  int nb, nsr, k, words;
   int32_t* err;
 };
-size_t slice_block_bytes(int k);
-cudaError_t launch_make_slices(const TileSet& x, const double* pool, void* slices, int k, int32_t* err,
-                               double scale, cudaStream_t st);
+size_t panel_record_bytes(int k);
+cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32_t* slot, const double* pool,
+                                void* data, uint8_t* head, int k, int32_t* err, double scale, cudaStream_t st);
+cudaError_t launch_popc_words(const uint32_t* bits, int64_t n, int32_t* cnt, cudaStream_t st);
+cudaError_t launch_panel_fill(const FullPattern& fp, int nb, const uint32_t* sbits, const int32_t* spos,
+                              uint32_t* index, cudaStream_t st);
 cudaError_t launch_absmax(const TileSet& x, const double* pool, unsigned long long* out, cudaStream_t st);
 cudaError_t launch_upper_bits(const TileSet& x, int nb, int words, uint32_t* bits, cudaStream_t st);
-cudaError_t launch_zero_half(void* p, int64_t n, cudaStream_t st);
 cudaError_t launch_super_bits(const FullPattern& fp, int nb, int nsr, uint32_t* sb, cudaStream_t st);
 int64_t super_order_size(int nsr);   // length of the (padded) launch-order index space
 cudaError_t launch_super_flags(const uint32_t* obits, int nb, int words, int nsr, int32_t* flag, cudaStream_t st);

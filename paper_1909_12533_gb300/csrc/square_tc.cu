@@ -15,18 +15,33 @@
 // with s + t <= k + 1 are used (k = 4: 10 MMAs per K step, error ~2^-44 per
 // element; k = 2 is the three-product hi+lo form).
 //
+// Operands are stored panel by panel: for a super-row R (tile rows 4R..4R+3)
+// and a K tile present in any of its rows, one record holds slice s of the 4
+// tiles as one contiguous 8 KB unit (the K-major layout the MMA reads, absent
+// tiles zero), so one bulk copy moves a whole 128 x 32 operand slice.  The
+// symmetric X~ needs one panel set for A and B alike.
+//
+// Most tiles of an SP2 iterate are small (density-matrix elements decay with
+// distance): a tile with max |x| < 2^-11 has T_1 = 0, below 2^-22 also T_2 = 0.
+// Each record notes its first slice that is not all zero.  For a K step the A
+// record starts at slice fA, the B record at fB, and only the pairs s >= fA,
+// t >= fB, s + t <= k + 1 are issued; only the slices they read are loaded.
+// Pairs left out multiply zeros, so the result is the same bit for bit.
+//
 // Data path per CTA (one 128 x 128 output super-tile = 4 x 4 tiles of 32):
-//   warp 0 lane 0: producer -- for every K tile in the union of the super-rows'
-//     patterns, one cp.async.bulk (TMA engine) of the k slices of each of the
-//     4 A tiles X~_{I+a,K} and 4 B tiles X~_{J+b,K} (8 KB each for k = 4) into a
-//     pipeline stage, completion tracked by an mbarrier transaction count;
-//     absent tiles come from a zero block.
+//   warp 0: producer -- for every K tile in the union of the super-rows'
+//     patterns (32 at a time, found from the super-row bitmaps, their record
+//     headers fetched one batch ahead), emits sub-steps of at most two A
+//     slices x two B slices: each sub-step is one pipeline stage filled by up
+//     to four 8 KB cp.async.bulk copies (completion tracked by an mbarrier
+//     transaction count), described by a small stage record.
 //   warp 1 lane 0: issues tcgen05.mma kind::f16 (M = 128, N = 128, K = 16) for
-//     every slice pair into the TMEM accumulator of its group, then
-//     tcgen05.commit frees the stage.
-//   all 8 warps: epilogue -- tcgen05.ld of the k accumulators, exact fixed-point
-//     combination, X_new = c0 I + c1 X~ + c2 S in FP64, per-tile ||X~ - S||^2,
-//     traces and ||X_new||^2, FP64 stores of the output tiles present.
+//     every slice pair of the record into the TMEM accumulator of its group,
+//     then tcgen05.commit frees the stage.
+//   all 8 warps: epilogue -- tcgen05.ld of the accumulators that were written,
+//     exact fixed-point combination, X_new = c0 I + c1 X~ + c2 S in FP64,
+//     per-tile ||X~ - S||^2, traces and ||X_new||^2, FP64 stores of the
+//     output tiles present.
 // Every wait is bounded; on timeout the kernel records an error flag, stops
 // issuing work and still frees its tensor memory.
 #include "sp2_internal.h"
@@ -144,53 +159,67 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 }
 
 // ------------------------------------------------------------------ slicing
-// One CTA per stored tile t (values at pool slot slot[t]): write both
-// orientations (the tile and its transpose) of the k slices, at index t, in
-// the interleaved K-major layout
-//   byte offset = g * (k * 512) + s * 512 + c * 128 + r * 16 + j * 2
-// for the element in row 8g + r, column 8c + j of slice s.
+// One CTA per panel record e: the 4 tiles of the record (index words from
+// k_panel_fill: compact tile index, bit 31 = use the stored tile transposed;
+// all ones = absent), sliced and written as k units of 8 KB,
+//   byte offset = s * 8192 + q * 2048 + g * 512 + c * 128 + r * 16 + j * 2
+// for the element in row 8g + r, column 8c + j of tile q, slice s.  The header
+// byte holds the first slice that is not all zero in any of the 4 tiles (k if
+// none) in bits 0-2 and the tiles present in bits 4-7.
 template <int K>
-__global__ void __launch_bounds__(256) k_make_slices(const int32_t* __restrict__ slot, const double* __restrict__ pool,
-                                                      __half* slices, int32_t* err, double inv_scale) {
-  // both orientations are assembled in shared memory, then written out with
-  // coalesced 16-byte stores (2 * k * 2 KB per tile)
-  __shared__ __align__(16) __half sm[2][K * TE];
-  const int64_t t = blockIdx.x;
-  const double* src = pool + (int64_t)slot[t] * TE;
+__global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ index, const int32_t* __restrict__ slot,
+                                                       const double* __restrict__ pool, __half* data,
+                                                       uint8_t* head, int32_t* err, double inv_scale) {
+  __shared__ __align__(16) __half sm[K * 4 * TE];
+  __shared__ uint32_t wnz[8];
+  const int64_t e = blockIdx.x;
+  const uint4 iw = index[e];
+  const uint32_t wd[4] = {iw.x, iw.y, iw.z, iw.w};
   constexpr int FIN = 11 * K - 1;                  // finest grid 2^-FIN
-  for (int q = threadIdx.x; q < TE; q += blockDim.x) {
-    const int r = q >> 5, c = q & 31;
-    double x = src[q] * inv_scale;
-    if (!(fabs(x) < 2.0)) {
-      if (err) atomicOr(err, 4);
-      x = fmin(fmax(x, -1.999), 1.999);
-    }
-    long long v = __double2ll_rn(x * (double)(1ll << FIN));
-    int T[K];
+  uint32_t nz = 0;                                 // bit s: slice s has a nonzero element
+  uint32_t pres = 0;
 #pragma unroll
-    for (int s = 0; s < K - 1; ++s) {
-      const int sh = 11 * (K - 1 - s);
-      const long long hi = (v + (1ll << (sh - 1))) >> sh;   // round to nearest (ties up)
-      T[s] = (int)hi;
-      v -= hi * (1ll << sh);
-    }
-    T[K - 1] = (int)v;
+  for (int q = 0; q < 4; ++q) {
+    const bool present = wd[q] != 0xFFFFFFFFu;
+    pres |= (present ? 1u : 0u) << q;
+    const bool tr = (wd[q] & REF_T) != 0;
+    const double* src = present ? pool + (int64_t)slot[wd[q] & ~REF_T] * TE : nullptr;
+    for (int i = threadIdx.x; i < TE; i += blockDim.x) {
+      // stored element (i / 32, i % 32) is element (r, c) of the panel's tile
+      const int r = tr ? (i & 31) : (i >> 5), c = tr ? (i >> 5) : (i & 31);
+      double x = present ? src[i] * inv_scale : 0.0;
+      if (!(fabs(x) < 2.0)) {
+        if (err) atomicOr(err, 4);
+        x = fmin(fmax(x, -1.999), 1.999);
+      }
+      long long v = __double2ll_rn(x * (double)(1ll << FIN));
+      int T[K];
 #pragma unroll
-    for (int s = 0; s < K; ++s) {
-      const __half h = __int2half_rn(T[s]);
-      sm[0][(r >> 3) * (K * 256) + s * 256 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7)] = h;
-      sm[1][(c >> 3) * (K * 256) + s * 256 + (r >> 3) * 64 + (c & 7) * 8 + (r & 7)] = h;
+      for (int s = 0; s < K - 1; ++s) {
+        const int sh = 11 * (K - 1 - s);
+        const long long hi = (v + (1ll << (sh - 1))) >> sh;   // round to nearest (ties up)
+        T[s] = (int)hi;
+        v -= hi * (1ll << sh);
+      }
+      T[K - 1] = (int)v;
+#pragma unroll
+      for (int s = 0; s < K; ++s) {
+        nz |= (T[s] != 0 ? 1u : 0u) << s;
+        sm[(s * 4 + q) * TE + (r >> 3) * 256 + (c >> 3) * 64 + (r & 7) * 8 + (c & 7)] = __int2half_rn(T[s]);
+      }
     }
   }
+  nz = __reduce_or_sync(0xffffffffu, nz);
+  if ((threadIdx.x & 31) == 0) wnz[threadIdx.x >> 5] = nz;
   __syncthreads();
-  const uint4* s4 = reinterpret_cast<const uint4*>(&sm[0][0]);
-  uint4* d4 = reinterpret_cast<uint4*>(slices + t * 2 * (int64_t)K * TE);
-  for (int i = threadIdx.x; i < 2 * K * TE / 8; i += blockDim.x) d4[i] = s4[i];
-}
-
-__global__ void k_zero_half(__half* p, int64_t n) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < n) p[i] = __float2half(0.0f);
+  if (threadIdx.x == 0) {
+    uint32_t m = 0;
+    for (int w = 0; w < 8; ++w) m |= wnz[w];
+    head[e] = (uint8_t)((m ? __ffs(m) - 1 : K) | (pres << 4));
+  }
+  const uint4* s4 = reinterpret_cast<const uint4*>(sm);
+  uint4* d4 = reinterpret_cast<uint4*>(data + e * (int64_t)(K * 4 * TE));
+  for (int i = threadIdx.x; i < K * 4 * TE / 8; i += blockDim.x) d4[i] = s4[i];
 }
 
 // super-row bitmap: OR of the 4 tile rows
@@ -254,14 +283,15 @@ __global__ void k_super_fill(const int32_t* __restrict__ flag, const int32_t* __
 }
 
 // ------------------------------------------------------------------ main kernel
-// One operand matrix of the product: both-triangle pattern, super-row bitmap
-// and FP16 slices (indexed by value slot).
+// One operand matrix of the product, as the kernel reads it: super-row
+// bitmaps; the record of (super-row R, K tile) is number spos[R][word] +
+// popcount of the lower bits of that word, with its header byte and k units
+// of FP16 slices (see k_panel_slices).
 struct TcOperand {
-  const uint32_t* bits;
-  const int32_t* frowptr;
-  const uint32_t* fref;
   const uint32_t* sbits;
-  const __half* slices;
+  const int32_t* spos;
+  const uint8_t* head;
+  const __half* data;
 };
 
 struct TcArgs {
@@ -272,7 +302,6 @@ struct TcArgs {
   const uint32_t* zref;
   const int32_t* zslot;     // value slot of Z's tile index (nullptr: identity)
   const double* zpool;
-  const __half* zero;       // K * 1024 zeros
   const uint32_t* obits;    // output pattern bitmap, upper tiles only
   const int32_t* orowptr;   // output tile row offsets
   const int32_t* list;      // active super-tiles, R * nsr + C
@@ -287,11 +316,22 @@ struct TcArgs {
   int32_t* err;
 };
 
+// A pipeline stage holds one sub-step: two A units and two B units, a unit
+// being one slice of a 4-tile panel (128 rows x 32, 8 KB, 8-row groups 512 B
+// apart).  A sub-step record (32 bits) tells the MMA issuer what it holds:
+//   bits 0-1 / 2-3: slices of A units 0 / 1, bits 4-5 / 6-7: of B units 0 / 1,
+//   bits 8-11: product mask, bit (2 i + j) for A unit i x B unit j,
+//   bit 12: end of the super-tile (no data).
+constexpr int UNIT_BYTES = 4 * SLICE_BYTES;
+constexpr int STAGE_BYTES = 4 * UNIT_BYTES;
+constexpr int STAGES = 6;
+constexpr uint32_t REC_END = 1u << 12;
+
+// record header byte: first nonzero slice (bits 0-2), tiles present (bits 4-7)
+constexpr uint32_t HEAD_NONE = 0x07u;   // header of a K index outside the step list
+
 template <int K>
 struct TcCfg {
-  static constexpr int TILE_BLOCK = K * SLICE_BYTES;          // k slices of one tile
-  static constexpr int STAGE_BYTES = 8 * TILE_BLOCK;          // 4 A + 4 B tiles
-  static constexpr int STAGES = (K >= 4) ? 3 : (K == 3 ? 4 : 6);
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
   // unit of the finest group, 2^-(11 (k + 1) - 2)
   static constexpr double UNIT = 1.0 / (double)(1ull << (11 * (K + 1) - 2));
@@ -300,18 +340,20 @@ struct TcCfg {
 template <int K>
 __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
   using Cfg = TcCfg<K>;
+  constexpr unsigned FULLW = 0xffffffffu;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* stage_base = smem_raw;
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + Cfg::STAGES * Cfg::STAGE_BYTES);
-  uint64_t* empty = full + Cfg::STAGES;
-  uint64_t* accb = empty + Cfg::STAGES;
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + STAGES * STAGE_BYTES);
+  uint64_t* empty = full + STAGES;
+  uint64_t* accb = empty + STAGES;
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
   int32_t* kcount = reinterpret_cast<int32_t*>(tmem_slot + 2);   // [16] triplets per tile
-  int32_t* status = kcount + 16;                                   // [0] timeout, [1] steps, [2] tile index
+  int32_t* status = kcount + 16;   // [0] timeout, [1] records, [2] tile index, [3] groups written
+  uint32_t* rec = reinterpret_cast<uint32_t*>(status + 4);        // [STAGES] sub-step records
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
-    for (int s = 0; s < Cfg::STAGES; ++s) {
+    for (int s = 0; s < STAGES; ++s) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
@@ -333,12 +375,11 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
   // Persistent: every CTA takes super-tiles from the work counter until none are
   // left.  Pipeline stages and barrier phases continue across tiles (step_base),
   // TMEM is allocated once; the accumulator barrier flips once per tile.
-  int step_base = 0;        // steps issued by this CTA before the current tile
-  uint64_t zero_slots = 0;  // producer: 8 bits per stage, slots that hold zeros
+  int step_base = 0;        // records issued by this CTA before the current tile
+  uint32_t zstages = 0;     // producer lane (unit, tile): stages whose slot holds zeros
   bool alive = true;
   for (uint32_t tile_iter = 0; alive; ++tile_iter) {
     if (threadIdx.x == 0) status[2] = atomicAdd(a.work, 1);
-    if (threadIdx.x < 16) kcount[threadIdx.x] = 0;
     __syncthreads();
     const int idx = status[2];
     if (idx >= total || status[0] != 0) break;
@@ -347,115 +388,191 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
     const int I0 = 4 * R, J0 = 4 * C;
 
     if (warp == 0) {
-      // ---------------- producer warp: lane q < 8 owns operand tile q (A rows
-      // I0..I0+3, then B rows J0..J0+3); the 8 tile lookups and bulk copies of a
-      // K step run in parallel, lane 0 arms the stage barrier first.
-      const int q = lane;
-      const int row = (q < 4) ? I0 + q : J0 + (q - 4);
-      const bool own = q < 8 && row < a.nb;
+      // ---------------- producer warp.  The record headers of 32 K steps are
+      // fetched at a time (lane j: step j), one batch ahead of their use;
+      // lanes 0-3 copy the units A0, A1, B0, B1 of a sub-step.
       int step = step_base;
       bool ok = true;
+      int kc = 0;   // lane t < 16: K steps with A tile t / 4 and B tile t % 4 both present
+      // one sub-step: wait for the stage, write the record, arm the barrier,
+      // start the copies (srcA / srcB: the K step's A and B panel records)
+      auto emit = [&](uint32_t rv, const __half* srcA, const __half* srcB) -> bool {
+        const int s = step % STAGES;
+        const uint32_t par = ((step / STAGES) & 1) ^ 1;
+        int good = 1;
+        if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
+        good = __shfl_sync(FULLW, good, 0);
+        if (!good) {
+          if (lane == 0) status[0] = 1;
+          return false;
+        }
+        bool ld = false;
+        const __half* src = nullptr;
+        if (!(rv & REC_END) && lane < 4) {
+          const uint32_t mask = (rv >> 8) & 0xFu;
+          const uint32_t umask = lane == 0 ? 0x3u : lane == 1 ? 0xCu : lane == 2 ? 0x5u : 0xAu;
+          ld = (mask & umask) != 0;
+          src = (lane < 2 ? srcA : srcB) + (int64_t)((rv >> (2 * lane)) & 3u) * (UNIT_BYTES / 2);
+        }
+        const uint32_t lm = __ballot_sync(FULLW, ld);
+        if (lane == 0) {
+          rec[s] = rv;
+          mbar_expect_tx(&full[s], (uint32_t)__popc(lm) * UNIT_BYTES);
+        }
+        __syncwarp();
+        if (ld) bulk_g2s(stage_base + s * STAGE_BYTES + lane * UNIT_BYTES, src, UNIT_BYTES, &full[s]);
+        ++step;
+        return true;
+      };
       for (int pass = 0; pass < 1 + a.two_pass && ok; ++pass) {
         // pass 0: A = P (rows I), B = Q (rows J); pass 1: A = Q, B = P
         const TcOperand& opA = pass == 0 ? a.P : a.Q;
         const TcOperand& opB = pass == 0 ? a.Q : a.P;
-        const TcOperand& mine = (q < 4) ? opA : opB;
-        const uint32_t* sA = opA.sbits + (int64_t)R * a.words;
-        const uint32_t* sB = opB.sbits + (int64_t)C * a.words;
-        int base = own ? mine.frowptr[row] : 0;
-        for (int w = 0; w < a.words && ok; ++w) {
-          uint32_t m = sA[w] & sB[w];
-          const uint32_t rb = own ? mine.bits[(int64_t)row * a.words + w] : 0u;
-          while (m) {
-            const int b = __ffs(m) - 1;
-            m &= m - 1;
-            const int s = step % Cfg::STAGES;
-            const uint32_t par = ((step / Cfg::STAGES) & 1) ^ 1;
-            // the tile lookup does not depend on the stage: issue it before waiting
-            const bool present = (rb >> b) & 1u;
-            const void* src = nullptr;
-            if (present) {
-              const uint32_t rf = mine.fref[base + __popc(rb & ((1u << b) - 1u))];
-              src = mine.slices + ((int64_t)(rf & ~REF_T) * 2 + ((rf & REF_T) ? 1 : 0)) * (int64_t)K * TE;
-            }
-            const uint32_t pres = __ballot_sync(0xffffffffu, q < 8 && present) & 0xFFu;
-            int good = 1;
-            if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
-            good = __shfl_sync(0xffffffffu, good, 0);
-            if (!good) { ok = false; if (lane == 0) status[0] = 1; break; }
-            unsigned char* dst = stage_base + s * Cfg::STAGE_BYTES;
-            // zero-fill absent slots that do not hold zeros yet (whole warp, 16-byte stores)
-            uint32_t fill = ~pres & ~(uint32_t)(zero_slots >> (8 * s)) & 0xFFu;
-            if (fill) {
-              while (fill) {
-                const int slot = __ffs(fill) - 1;
-                fill &= fill - 1;
-                uint4* z4 = reinterpret_cast<uint4*>(dst + slot * Cfg::TILE_BLOCK);
-                for (int i = lane; i < Cfg::TILE_BLOCK / 16; i += 32) z4[i] = make_uint4(0u, 0u, 0u, 0u);
-              }
-              asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-              __syncwarp();
-            }
-            zero_slots = (zero_slots & ~(0xFFull << (8 * s))) | ((uint64_t)(~pres & 0xFFu) << (8 * s));
-            if (lane == 0) mbar_expect_tx(&full[s], (uint32_t)__popc(pres) * Cfg::TILE_BLOCK);
-            __syncwarp();
-            if (q < 8 && present) bulk_g2s(dst + q * Cfg::TILE_BLOCK, src, Cfg::TILE_BLOCK, &full[s]);
-            if (lane == 0) {
-              const int amask = pres & 0xF, bmask = (pres >> 4) & 0xF;
-              for (int x = 0; x < 4; ++x)
-                for (int y = 0; y < 4; ++y)
-                  if (((amask >> x) & 1) && ((bmask >> y) & 1)) kcount[x * 4 + y] += 1;
-            }
-            ++step;
+        const int64_t offA = (int64_t)R * a.words, offB = (int64_t)C * a.words;
+        for (int w0 = 0; w0 < a.words && ok; w0 += 32) {
+          // lane L holds word w0 + L of both super-rows; the K steps are the set
+          // bits of ma & mb, numbered through the inclusive prefix incl
+          const int wl = w0 + lane;
+          uint32_t ma = 0u, mb = 0u;
+          int pa = 0, pb = 0;
+          if (wl < a.words) {
+            ma = opA.sbits[offA + wl];
+            mb = opB.sbits[offB + wl];
+            pa = opA.spos[offA + wl];
+            pb = opB.spos[offB + wl];
           }
-          base += __popc(rb);
+          const uint32_t mw = ma & mb;
+          const int cnt = __popc(mw);
+          int incl = cnt;
+#pragma unroll
+          for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(FULLW, incl, o);
+            if (lane >= o) incl += v;
+          }
+          const int total = __shfl_sync(FULLW, incl, 31);
+          const int excl = incl - cnt;
+          // records (A, B) of step j of this chunk and their header bytes
+          auto fetch = [&](int j, int& ea, int& eb, uint32_t& ha, uint32_t& hb) {
+            ea = eb = 0;
+            ha = hb = HEAD_NONE;
+            int L = 0;   // lanes whose prefix is <= j: the word lane of step j
+#pragma unroll
+            for (int h = 16; h > 0; h >>= 1)
+              if (__shfl_sync(FULLW, incl, L + h - 1) <= j) L += h;
+            const int Lc = min(L, 31);
+            const uint32_t mL = __shfl_sync(FULLW, mw, Lc);
+            const uint32_t maL = __shfl_sync(FULLW, ma, Lc);
+            const uint32_t mbL = __shfl_sync(FULLW, mb, Lc);
+            const int paL = __shfl_sync(FULLW, pa, Lc);
+            const int pbL = __shfl_sync(FULLW, pb, Lc);
+            const int exL = __shfl_sync(FULLW, excl, Lc);
+            if (j < total) {
+              uint32_t m = mL;
+              for (int r = j - exL; r > 0; --r) m &= m - 1;
+              const uint32_t below = (1u << (__ffs(m) - 1)) - 1u;
+              ea = paL + __popc(maL & below);
+              eb = pbL + __popc(mbL & below);
+              ha = opA.head[ea];
+              hb = opB.head[eb];
+            }
+          };
+          int ea, eb;
+          uint32_t ha, hb;
+          fetch(lane, ea, eb, ha, hb);
+          for (int jb = 0; jb < total && ok; jb += 32) {
+            int ea_n, eb_n;
+            uint32_t ha_n, hb_n;
+            fetch(jb + 32 + lane, ea_n, eb_n, ha_n, hb_n);   // next batch, in flight during this one
+            // triplet counts: K steps of this batch with A tile x and B tile y present
+            const uint32_t pa4 = (ha >> 4) & 0xFu, pb4 = (hb >> 4) & 0xFu;
+#pragma unroll
+            for (int t = 0; t < 16; ++t) {
+              const int c16 = __popc(__ballot_sync(FULLW, (pa4 >> (t >> 2)) & (pb4 >> (t & 3)) & 1u));
+              if (lane == t) kc += c16;
+            }
+            // only K steps with at least one slice pair s + t <= K - 1
+            const int fa = (int)(ha & 7u), fb = (int)(hb & 7u);
+            uint32_t act = __ballot_sync(FULLW, fa + fb <= K - 1);
+            while (act && ok) {
+              const int j = __ffs(act) - 1;
+              act &= act - 1;
+              const int fA = __shfl_sync(FULLW, fa, j), fB = __shfl_sync(FULLW, fb, j);
+              const int eA = __shfl_sync(FULLW, ea, j), eB = __shfl_sync(FULLW, eb, j);
+              const __half* srcA = opA.data + (int64_t)eA * (K * UNIT_BYTES / 2);
+              const __half* srcB = opB.data + (int64_t)eB * (K * UNIT_BYTES / 2);
+              // pairs s >= fA, t >= fB, s + t <= K - 1, two A and two B slices per sub-step
+              for (int a0 = fA; a0 + fB <= K - 1 && ok; a0 += 2) {
+                for (int b0 = fB; a0 + b0 <= K - 1 && ok; b0 += 2) {
+                  uint32_t mask = 0;
+                  for (int i = 0; i < 2; ++i)
+                    for (int jj = 0; jj < 2; ++jj)
+                      if (a0 + i + b0 + jj <= K - 1) mask |= 1u << (2 * i + jj);
+                  const uint32_t rv = (uint32_t)a0 | ((uint32_t)min(a0 + 1, K - 1) << 2) | ((uint32_t)b0 << 4) |
+                                      ((uint32_t)min(b0 + 1, K - 1) << 6) | (mask << 8);
+                  ok = emit(rv, srcA, srcB);
+                }
+              }
+            }
+            ea = ea_n;
+            eb = eb_n;
+            ha = ha_n;
+            hb = hb_n;
+          }
         }
       }
+      if (ok) ok = emit(REC_END, nullptr, nullptr);
       if (lane == 0) status[1] = step - step_base;
+      if (lane < 16) kcount[lane] = kc;
     } else if (warp == 1 && lane == 0) {
-      // ---------------- MMA issuer
-      int nsteps = 0;
-      for (int w = 0; w < a.words; ++w)
-        nsteps += __popc(a.P.sbits[(int64_t)R * a.words + w] & a.Q.sbits[(int64_t)C * a.words + w]);
-      if (a.two_pass)
-        for (int w = 0; w < a.words; ++w)
-          nsteps += __popc(a.Q.sbits[(int64_t)R * a.words + w] & a.P.sbits[(int64_t)C * a.words + w]);
+      // ---------------- MMA issuer: the records of this tile up to the end record
+      uint32_t written = 0;       // group accumulators written in this tile
+      unsigned long long nprod = 0;
       bool ok = true;
-      for (int ls = 0; ls < nsteps; ++ls) {
+      for (int ls = 0;; ++ls) {
         const int step = step_base + ls;
-        const int s = step % Cfg::STAGES;
-        const uint32_t par = (step / Cfg::STAGES) & 1;
-        if (!mbar_wait(&full[s], par)) { ok = false; status[0] = 1; break; }
+        const int s = step % STAGES;
+        const uint32_t par = (step / STAGES) & 1;
+        if (!mbar_wait(&full[s], par)) { ok = false; break; }
         tc_fence_after();
-        const uint32_t sA = smem_u32(stage_base + s * Cfg::STAGE_BYTES);
-        const uint32_t sB = sA + 4 * Cfg::TILE_BLOCK;
+        const uint32_t rv = rec[s];
+        if (rv & REC_END) {
+          mma_commit(&empty[s]);
+          break;
+        }
+        const uint32_t sbase = smem_u32(stage_base + s * STAGE_BYTES);
 #pragma unroll
-        for (int ps = 0; ps < K; ++ps) {
+        for (int i = 0; i < 2; ++i) {
 #pragma unroll
-          for (int pt = 0; pt < K; ++pt) {
-            if (ps + pt > K - 1) continue;          // s + t <= k + 1 (1-based)
-            const uint32_t dcol = tmem + (uint32_t)((ps + pt) * ST);
+          for (int j = 0; j < 2; ++j) {
+            if (!((rv >> (8 + 2 * i + j)) & 1u)) continue;
+            const int g = (int)((rv >> (2 * i)) & 3u) + (int)((rv >> (4 + 2 * j)) & 3u);
+            const uint32_t dcol = tmem + (uint32_t)(g * ST);
+            const uint32_t acc = (written >> g) & 1u;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
-              const uint64_t ad = make_desc(sA + ps * 512 + kk * 256, 128, K * 512);
-              const uint64_t bd = make_desc(sB + pt * 512 + kk * 256, 128, K * 512);
-              // the first MMA into each group accumulator of a tile (its first
-              // step, first K half, ps = 0) overwrites it; all others accumulate
-              mma_f16(dcol, ad, bd, (ls > 0 || kk > 0 || ps > 0) ? 1u : 0u);
+              const uint64_t ad = make_desc(sbase + i * UNIT_BYTES + kk * 256, 128, 512);
+              const uint64_t bd = make_desc(sbase + (2 + j) * UNIT_BYTES + kk * 256, 128, 512);
+              // the first MMA into a group accumulator of a tile overwrites it
+              mma_f16(dcol, ad, bd, (kk > 0 || acc) ? 1u : 0u);
             }
+            written |= 1u << g;
+            ++nprod;
           }
         }
         mma_commit(&empty[s]);
       }
       if (!ok) status[0] = 1;
+      status[3] = (int32_t)written;
+      // slice-pair products issued (each 2 MMAs of 128 x 128 x 16)
+      if (a.err && nprod) atomicAdd(reinterpret_cast<unsigned long long*>(a.err + 2), nprod);
       mma_commit(accb);   // arrives once every MMA issued above has completed
     }
     __syncwarp();
     __syncthreads();
 
     // ---------------- epilogue (all 8 warps)
-    const int nsteps = status[1];
-    step_base += nsteps;
+    step_base += status[1];
+    const uint32_t written = (uint32_t)status[3];
     // block-uniform outcome of the bounded wait (a late completion must not split the CTA)
     const bool acc_ok = !__syncthreads_or(!mbar_wait(accb, tile_iter & 1u) || status[0] != 0);
     if (!acc_ok) alive = false;
@@ -513,15 +630,14 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
           }
         }
         float g[K][16];
-        if (nsteps > 0) {
 #pragma unroll
-          for (int gg = 0; gg < K; ++gg)
+        for (int gg = 0; gg < K; ++gg) {
+          if ((written >> gg) & 1u) {   // block-uniform: groups no product reached are zero
             tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(gg * ST + col0), g[gg]);
-        } else {
-#pragma unroll
-          for (int gg = 0; gg < K; ++gg)
+          } else {
 #pragma unroll
             for (int i = 0; i < 16; ++i) g[gg][i] = 0.0f;
+          }
         }
         if (oidx < 0) continue;
         double* O = a.opool + (int64_t)oidx * TE;
@@ -564,11 +680,7 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
         a.part.ktiles[oidx] = kcount[quarter * 4 + b];
       }
     }
-    if (threadIdx.x == 0 && a.err) {
-      if (!acc_ok) atomicOr(a.err, 1);
-      // K steps issued (hardware MMA work = steps * pairs * 2 MMAs of 128x128x16)
-      atomicAdd(reinterpret_cast<unsigned long long*>(a.err + 2), (unsigned long long)nsteps);
-    }
+    if (threadIdx.x == 0 && a.err && !acc_ok) atomicOr(a.err, 1);
     // TMEM reads of this tile are complete before the next tile's MMAs start
     tc_fence_before();
     __syncthreads();
@@ -586,16 +698,60 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 
 }  // namespace
 
-size_t slice_block_bytes(int k) { return (size_t)k * SLICE_BYTES; }
+size_t panel_record_bytes(int k) { return (size_t)k * UNIT_BYTES; }
 
-cudaError_t launch_make_slices(const TileSet& x, const double* pool, void* slices, int k, int32_t* err,
-                               double scale, cudaStream_t st) {
-  if (x.nnzb == 0) return cudaSuccess;
-  __half* s = static_cast<__half*>(slices);
+cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32_t* slot, const double* pool,
+                                void* data, uint8_t* head, int k, int32_t* err, double scale, cudaStream_t st) {
+  if (nrec == 0) return cudaSuccess;
+  const uint4* ix = reinterpret_cast<const uint4*>(index);
+  __half* d = static_cast<__half*>(data);
   const double inv = 1.0 / scale;   // scale is a power of two: exact
-  if (k == 2) { ++g_launches; k_make_slices<2><<<(unsigned)x.nnzb, 256, 0, st>>>(x.slot, pool, s, err, inv); }
-  else if (k == 3) { ++g_launches; k_make_slices<3><<<(unsigned)x.nnzb, 256, 0, st>>>(x.slot, pool, s, err, inv); }
-  else { ++g_launches; k_make_slices<4><<<(unsigned)x.nnzb, 256, 0, st>>>(x.slot, pool, s, err, inv); }
+  const unsigned g = (unsigned)nrec;
+  ++g_launches;
+  if (k == 2) k_panel_slices<2><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, inv);
+  else if (k == 3) k_panel_slices<3><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, inv);
+  else k_panel_slices<4><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, inv);
+  return cudaGetLastError();
+}
+
+// number of set bits of each word
+__global__ void k_popc_words(const uint32_t* __restrict__ bits, int64_t n, int32_t* cnt) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) cnt[i] = __popc(bits[i]);
+}
+
+// Record index words: one warp per tile row; every stored tile (row, K) of the
+// both-triangle pattern writes its word (slot row % 4) of the record of
+// (super-row row / 4, K): compact tile index, bit 31 when the stored tile is
+// used transposed.  Words start all ones (absent).
+__global__ void k_panel_fill(const int32_t* __restrict__ frowptr, const int32_t* __restrict__ fcol,
+                             const uint32_t* __restrict__ fref, const uint32_t* __restrict__ sbits,
+                             const int32_t* __restrict__ spos, int nb, int words, uint32_t* index) {
+  const int row = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (row >= nb) return;
+  const int64_t o = (int64_t)(row >> 2) * words;
+  for (int p = frowptr[row] + lane; p < frowptr[row + 1]; p += 32) {
+    const int k = fcol[p];
+    const int w = k >> 5;
+    const int64_t e = spos[o + w] + __popc(sbits[o + w] & ((1u << (k & 31)) - 1u));
+    index[e * 4 + (row & 3)] = fref[p];
+  }
+}
+
+cudaError_t launch_popc_words(const uint32_t* bits, int64_t n, int32_t* cnt, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  ++g_launches;
+  k_popc_words<<<grid_for(n, 256), 256, 0, st>>>(bits, n, cnt);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_panel_fill(const FullPattern& fp, int nb, const uint32_t* sbits, const int32_t* spos,
+                              uint32_t* index, cudaStream_t st) {
+  if (nb == 0) return cudaSuccess;
+  ++g_launches;
+  k_panel_fill<<<grid_for((int64_t)nb * 32, 256), 256, 0, st>>>(fp.rowptr, fp.col, fp.ref, sbits, spos, nb, fp.words,
+                                                                 index);
   return cudaGetLastError();
 }
 
@@ -636,12 +792,6 @@ cudaError_t launch_upper_bits(const TileSet& x, int nb, int words, uint32_t* bit
   return cudaGetLastError();
 }
 
-cudaError_t launch_zero_half(void* p, int64_t n, cudaStream_t st) {
-  ++g_launches;
-  k_zero_half<<<grid_for(n, 256), 256, 0, st>>>(static_cast<__half*>(p), n);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_super_bits(const FullPattern& fp, int nb, int nsr, uint32_t* sb, cudaStream_t st) {
   ++g_launches;
   k_super_bits<<<grid_for((int64_t)nsr * fp.words, 256), 256, 0, st>>>(fp.bits, nb, fp.words, nsr, sb);
@@ -666,15 +816,14 @@ cudaError_t launch_super_fill(const int32_t* flag, const int32_t* pos, int64_t n
 cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   if (L.nsuper == 0) return cudaSuccess;
   TcArgs a;
-  a.P = TcOperand{L.P->bits, L.P->rowptr, L.P->ref, L.Psbits, static_cast<const __half*>(L.Pslices)};
-  a.Q = TcOperand{L.Q->bits, L.Q->rowptr, L.Q->ref, L.Qsbits, static_cast<const __half*>(L.Qslices)};
+  a.P = TcOperand{L.P.sbits, L.P.spos, L.P.head, static_cast<const __half*>(L.P.data)};
+  a.Q = TcOperand{L.Q.sbits, L.Q.spos, L.Q.head, static_cast<const __half*>(L.Q.data)};
   a.two_pass = L.two_pass ? 1 : 0;
   a.zbits = L.Z->bits; a.zrowptr = L.Z->rowptr; a.zref = L.Z->ref; a.zslot = L.zslot; a.zpool = L.zpool;
-  a.zero = static_cast<const __half*>(L.zero);
   a.obits = L.obits; a.orowptr = L.orowptr; a.list = L.list; a.count = L.count; a.work = L.work;
   a.opool = L.opool;
   a.part = L.part; a.c0 = L.c0; a.c1 = L.c1; a.c2 = L.c2; a.scale = L.scale; a.n = L.n; a.nb = L.nb;
-  a.words = L.P->words; a.nsr = L.nsr; a.err = L.err;
+  a.words = L.words; a.nsr = L.nsr; a.err = L.err;
   cudaError_t e = cudaSuccess;
   switch (L.k) {
     case 2:
