@@ -264,7 +264,7 @@ struct sp2_ctx {
   Buf p_e2, p_trS, p_trX, p_n2, p_kt, keep, scanbuf, scantmp, twork, rowlo, rowhi;
   Buf dsc, dcnt, d2;
   OpBufs opx, opy;   // tensor-core operands (the adjoint uses both)
-  Buf sflag, spos, slist, errflag, scount;
+  Buf sflag, spos, slist, errflag, scount, tcscratch;
   // adjoint
   std::vector<Rec> recs;
   std::vector<Buf> seg;
@@ -290,7 +290,7 @@ struct sp2_ctx {
                   &fp_col, &fp_ref, &counts, &p_e2, &p_trS, &p_trX, &p_n2, &p_kt, &keep, &scanbuf, &scantmp,
                   &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &opx.sbits,
                   &opx.cnt, &opx.spos, &opx.index, &opx.head, &opx.data, &opy.sbits, &opy.cnt, &opy.spos,
-                  &opy.index, &opy.head, &opy.data, &sflag, &spos, &slist, &errflag, &scount, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
+                  &opy.index, &opy.head, &opy.data, &sflag, &spos, &slist, &errflag, &scount, &tcscratch, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
                   &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax};
     for (Buf* b : all) bufs.push_back(b);
   }
@@ -562,6 +562,8 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   L.nsr = nsr;
   L.k = k;
   L.words = c->words;
+  c->ensure(c->tcscratch, (size_t)nsuper * 2 * 128 * 128 * 8);
+  L.scratch = c->tcscratch.p;
   L.err = c->errflag.as<int32_t>();
   c->ck(cudaEventRecord(c->evs0, c->st), "event");
   c->ck(launch_square_tc(L, c->st), "square tc");

@@ -143,6 +143,7 @@ struct TcLaunch {
   int64_t n;
   int nb, nsr, k, words;
   int32_t* err;
+  void* scratch;             // nsuper * 2 * 128 * 128 int64 (epilogue staging, two tiles per CTA)
 };
 size_t panel_record_bytes(int k);
 cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32_t* slot, const double* pool,

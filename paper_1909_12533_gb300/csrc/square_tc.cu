@@ -68,6 +68,10 @@ __device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
                : "memory");
 }
 
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
 __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
@@ -112,6 +116,29 @@ __device__ __forceinline__ long long f32_int_to_ll(float x) {
   const int ih = __float_as_int(hi + 12582912.0f) - 0x4B400000;
   const int il = __float_as_int(lo + 12582912.0f) - 0x4B400000;
   return (long long)ih * 2048 + il;
+}
+
+// Float of a double from its high word (sign, exponent, 20 mantissa bits):
+// relative error below 2^-20, |x| < 2^-126 gives 0.  Integer pipes only.
+__device__ __forceinline__ float f64_hi_to_f32(double x) {
+  const uint32_t hi = (uint32_t)__double2hiint(x);
+  const uint32_t e = (hi >> 20) & 0x7FFu;
+  const uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3);
+  return __uint_as_float(e > 896u ? f : 0u);
+}
+
+// x * 2^k, exact, by exponent arithmetic on the high word; x an integer-valued
+// double (0 or |x| >= 1) and a normal result.
+__device__ __forceinline__ double int_times_pow2(double x, int k) {
+  const int hi = __double2hiint(x);
+  return (hi & 0x7FFFFFFF) == 0 ? x : __hiloint2double(hi + (k << 20), __double2loint(x));
+}
+
+// 2 z exactly (an exponent increment for normal z; the FP64 add otherwise).
+__device__ __forceinline__ double twice(double z) {
+  const int hi = __double2hiint(z);
+  const int e = (hi >> 20) & 0x7FF;
+  return (e != 0 && e < 0x7FE) ? __hiloint2double(hi + (1 << 20), __double2loint(z)) : z + z;
 }
 
 // Shared-memory matrix descriptor, no swizzle, K-major canonical layout:
@@ -314,6 +341,7 @@ struct TcArgs {
   int64_t n;
   int nb, words, nsr;
   int32_t* err;
+  long long* scratch;       // per CTA, 2 slots: 128 x 128 fixed-point sums of a tile in its epilogue
 };
 
 // A pipeline stage holds one sub-step: two A units and two B units, a unit
@@ -321,11 +349,14 @@ struct TcArgs {
 // apart).  A sub-step record (32 bits) tells the MMA issuer what it holds:
 //   bits 0-1 / 2-3: slices of A units 0 / 1, bits 4-5 / 6-7: of B units 0 / 1,
 //   bits 8-11: product mask, bit (2 i + j) for A unit i x B unit j,
-//   bit 12: end of the super-tile (no data).
+//   bit 12: end of the super-tile, bit 13: no more super-tiles (no data).
 constexpr int UNIT_BYTES = 4 * SLICE_BYTES;
 constexpr int STAGE_BYTES = 4 * UNIT_BYTES;
 constexpr int STAGES = 6;
 constexpr uint32_t REC_END = 1u << 12;
+constexpr int EPI_WARPS = 8;                       // epilogue warps 2..9
+constexpr int TC_THREADS = 32 * (2 + EPI_WARPS);   // + producer warp 0, MMA warp 1
+constexpr uint32_t REC_LAST = 1u << 13;   // no more super-tiles (no data)
 
 // record header byte: first nonzero slice (bits 0-2), tiles present (bits 4-7)
 constexpr uint32_t HEAD_NONE = 0x07u;   // header of a K index outside the step list
@@ -338,18 +369,24 @@ struct TcCfg {
 };
 
 template <int K>
-__global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
+__global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   using Cfg = TcCfg<K>;
   constexpr unsigned FULLW = 0xffffffffu;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* stage_base = smem_raw;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* accb = empty + STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(accb + 1);
-  int32_t* kcount = reinterpret_cast<int32_t*>(tmem_slot + 2);   // [16] triplets per tile
-  int32_t* status = kcount + 16;   // [0] timeout, [1] records, [2] tile index, [3] groups written
-  uint32_t* rec = reinterpret_cast<uint32_t*>(status + 4);        // [STAGES] sub-step records
+  uint64_t* acc_full = empty + STAGES;     // [2] MMAs of the tile done (commit) + group map written
+  uint64_t* tile_full = acc_full + 2;      // [2] tile slot written by the producer
+  uint64_t* tile_empty = tile_full + 2;    // [2] epilogue done with the tile slot (one arrive per warp)
+  uint64_t* drain = tile_empty + 2;        // MMAs issued before the exit are complete
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  int32_t* tslot = reinterpret_cast<int32_t*>(tmem_slot + 2);      // [2] super-tile list index, -1: none
+  int32_t* kcount = tslot + 2;                                      // [2][16] triplets per output tile
+  uint32_t* gmap = reinterpret_cast<uint32_t*>(kcount + 32);       // [2] groups written, block of each
+  uint32_t* rec = gmap + 2;                                         // [STAGES] sub-step records
+  int32_t* status = reinterpret_cast<int32_t*>(rec + STAGES);      // [0] a wait timed out
+  uint32_t* tfree = reinterpret_cast<uint32_t*>(status + 1);       // TMEM blocks released (warps x tiles)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -357,9 +394,15 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    mbar_init(accb, 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 2);
+      mbar_init(&tile_full[b], 1);
+      mbar_init(&tile_empty[b], EPI_WARPS);
+    }
+    mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     status[0] = 0;
+    *tfree = 0u;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
@@ -372,58 +415,72 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
   const uint32_t tmem = *tmem_slot;
   const int total = *a.count;
 
-  // Persistent: every CTA takes super-tiles from the work counter until none are
-  // left.  Pipeline stages and barrier phases continue across tiles (step_base),
-  // TMEM is allocated once; the accumulator barrier flips once per tile.
-  int step_base = 0;        // records issued by this CTA before the current tile
-  uint32_t zstages = 0;     // producer lane (unit, tile): stages whose slot holds zeros
-  bool alive = true;
-  for (uint32_t tile_iter = 0; alive; ++tile_iter) {
-    if (threadIdx.x == 0) status[2] = atomicAdd(a.work, 1);
-    __syncthreads();
-    const int idx = status[2];
-    if (idx >= total || status[0] != 0) break;
-    const int st = a.list[idx];
-    const int R = st / a.nsr, C = st % a.nsr;
-    const int I0 = 4 * R, J0 = 4 * C;
-
-    if (warp == 0) {
-      // ---------------- producer warp.  The record headers of 32 K steps are
-      // fetched at a time (lane j: step j), one batch ahead of their use;
-      // lanes 0-3 copy the units A0, A1, B0, B1 of a sub-step.
-      int step = step_base;
-      bool ok = true;
-      int kc = 0;   // lane t < 16: K steps with A tile t / 4 and B tile t % 4 both present
-      // one sub-step: wait for the stage, write the record, arm the barrier,
-      // start the copies (srcA / srcB: the K step's A and B panel records)
-      auto emit = [&](uint32_t rv, const __half* srcA, const __half* srcB) -> bool {
-        const int s = step % STAGES;
-        const uint32_t par = ((step / STAGES) & 1) ^ 1;
-        int good = 1;
-        if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
-        good = __shfl_sync(FULLW, good, 0);
-        if (!good) {
-          if (lane == 0) status[0] = 1;
-          return false;
-        }
-        bool ld = false;
-        const __half* src = nullptr;
-        if (!(rv & REC_END) && lane < 4) {
-          const uint32_t mask = (rv >> 8) & 0xFu;
-          const uint32_t umask = lane == 0 ? 0x3u : lane == 1 ? 0xCu : lane == 2 ? 0x5u : 0xAu;
-          ld = (mask & umask) != 0;
-          src = (lane < 2 ? srcA : srcB) + (int64_t)((rv >> (2 * lane)) & 3u) * (UNIT_BYTES / 2);
-        }
-        const uint32_t lm = __ballot_sync(FULLW, ld);
+  // Persistent and warp-specialised: the producer (warp 0) takes super-tiles
+  // from the work counter and streams their operand slices; the MMA issuer
+  // (warp 1) accumulates each tile in TMEM blocks of 128 columns taken on
+  // first use; the epilogue (warps 4-7) finishes tile i while tiles i + 1 and
+  // i + 2 are being loaded and multiplied.  Tiles pass through two slots.
+  if (warp == 0) {
+    // ---------------- producer warp.  The record headers of 32 K steps are
+    // fetched at a time (lane j: step j), one batch ahead of their use;
+    // lanes 0-3 copy the units A0, A1, B0, B1 of a sub-step.
+    int step = 0;
+    bool ok = true;
+    // one sub-step: wait for the stage, write the record, arm the barrier,
+    // start the copies (srcA / srcB: the K step's A and B panel records)
+    auto emit = [&](uint32_t rv, const __half* srcA, const __half* srcB) -> bool {
+      const int s = step % STAGES;
+      const uint32_t par = ((step / STAGES) & 1) ^ 1;
+      int good = 1;
+      if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
+      good = __shfl_sync(FULLW, good, 0);
+      if (!good) {
+        if (lane == 0) status[0] = 1;
+        return false;
+      }
+      bool ld = false;
+      const __half* src = nullptr;
+      if (!(rv & (REC_END | REC_LAST)) && lane < 4) {
+        const uint32_t mask = (rv >> 8) & 0xFu;
+        const uint32_t umask = lane == 0 ? 0x3u : lane == 1 ? 0xCu : lane == 2 ? 0x5u : 0xAu;
+        ld = (mask & umask) != 0;
+        src = (lane < 2 ? srcA : srcB) + (int64_t)((rv >> (2 * lane)) & 3u) * (UNIT_BYTES / 2);
+      }
+      const uint32_t lm = __ballot_sync(FULLW, ld);
+      if (lane == 0) {
+        rec[s] = rv;
+        mbar_expect_tx(&full[s], (uint32_t)__popc(lm) * UNIT_BYTES);
+      }
+      __syncwarp();
+      if (ld) bulk_g2s(stage_base + s * STAGE_BYTES + lane * UNIT_BYTES, src, UNIT_BYTES, &full[s]);
+      ++step;
+      return true;
+    };
+    for (int it = 0; ok; ++it) {
+      const int b = it & 1;
+      // the slot's previous tile (it - 2) has left the epilogue
+      int good = 1;
+      if (lane == 0) good = mbar_wait(&tile_empty[b], (((uint32_t)it >> 1) & 1u) ^ 1u) ? 1 : 0;
+      good = __shfl_sync(FULLW, good, 0);
+      if (!good) {
+        if (lane == 0) status[0] = 1;
+        break;
+      }
+      int idx = 0;
+      if (lane == 0) idx = atomicAdd(a.work, 1);
+      idx = __shfl_sync(FULLW, idx, 0);
+      if (idx >= total || *(volatile int32_t*)status != 0) {
+        // no more tiles: tell the epilogue (slot) and the MMA issuer (record)
         if (lane == 0) {
-          rec[s] = rv;
-          mbar_expect_tx(&full[s], (uint32_t)__popc(lm) * UNIT_BYTES);
+          tslot[b] = -1;
+          mbar_arrive(&tile_full[b]);
         }
-        __syncwarp();
-        if (ld) bulk_g2s(stage_base + s * STAGE_BYTES + lane * UNIT_BYTES, src, UNIT_BYTES, &full[s]);
-        ++step;
-        return true;
-      };
+        emit(REC_LAST, nullptr, nullptr);
+        break;
+      }
+      const int stile = a.list[idx];
+      const int R = stile / a.nsr, C = stile % a.nsr;
+      int kc = 0;   // lane t < 16: K steps with A tile t / 4 and B tile t % 4 both present
       for (int pass = 0; pass < 1 + a.two_pass && ok; ++pass) {
         // pass 0: A = P (rows I), B = Q (rows J); pass 1: A = Q, B = P
         const TcOperand& opA = pass == 0 ? a.P : a.Q;
@@ -521,22 +578,48 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
         }
       }
       if (ok) ok = emit(REC_END, nullptr, nullptr);
-      if (lane == 0) status[1] = step - step_base;
-      if (lane < 16) kcount[lane] = kc;
-    } else if (warp == 1 && lane == 0) {
-      // ---------------- MMA issuer: the records of this tile up to the end record
-      uint32_t written = 0;       // group accumulators written in this tile
-      unsigned long long nprod = 0;
-      bool ok = true;
-      for (int ls = 0;; ++ls) {
-        const int step = step_base + ls;
+      if (lane < 16) kcount[b * 16 + lane] = kc;
+      if (lane == 0) tslot[b] = idx;
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tile_full[b]);   // release: slot and counts visible to the epilogue
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer.  TMEM is four blocks of 128 columns; a group
+    // accumulator of a tile takes a free block on its first product, and the
+    // blocks of a tile return to the pool once all epilogue warps have read
+    // them (tfree counts warp releases, EPI_WARPS per tile, in tile order).
+    int step = 0;
+    uint32_t free_mask = 0xFu;
+    uint32_t pend0 = 0u, pend1 = 0u;   // blocks held by the tile in slot 0 / 1 until released
+    int released = 0;              // tiles whose blocks are back in free_mask
+    unsigned long long nprod = 0;
+    bool ok = true, done = false;
+    // take back the blocks of the oldest tile that still holds some; false on timeout
+    auto reclaim = [&]() -> bool {
+      const unsigned long long t0 = now_ns();
+      while (*(volatile uint32_t*)tfree < (uint32_t)EPI_WARPS * (uint32_t)(released + 1)) {
+        if (now_ns() - t0 > WAIT_NS) return false;
+      }
+      __threadfence_block();
+      tc_fence_after();
+      if (released & 1) { free_mask |= pend1; pend1 = 0u; }
+      else { free_mask |= pend0; pend0 = 0u; }
+      ++released;
+      return true;
+    };
+    for (int it = 0; ok && !done; ++it) {
+      const int b = it & 1;
+      uint32_t written = 0, gblk = 0, used = 0;
+      for (;;) {
         const int s = step % STAGES;
         const uint32_t par = (step / STAGES) & 1;
+        ++step;
         if (!mbar_wait(&full[s], par)) { ok = false; break; }
         tc_fence_after();
         const uint32_t rv = rec[s];
-        if (rv & REC_END) {
+        if (rv & (REC_END | REC_LAST)) {
           mma_commit(&empty[s]);
+          done = (rv & REC_LAST) != 0;
           break;
         }
         const uint32_t sbase = smem_u32(stage_base + s * STAGE_BYTES);
@@ -546,7 +629,15 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
           for (int j = 0; j < 2; ++j) {
             if (!((rv >> (8 + 2 * i + j)) & 1u)) continue;
             const int g = (int)((rv >> (2 * i)) & 3u) + (int)((rv >> (4 + 2 * j)) & 3u);
-            const uint32_t dcol = tmem + (uint32_t)(g * ST);
+            if (!((written >> g) & 1u)) {
+              while (free_mask == 0u && ok) ok = reclaim();
+              if (!ok) break;
+              const uint32_t blk = (uint32_t)(__ffs(free_mask) - 1);
+              free_mask &= ~(1u << blk);
+              used |= 1u << blk;
+              gblk |= blk << (2 * g);
+            }
+            const uint32_t dcol = tmem + ((gblk >> (2 * g)) & 3u) * ST;
             const uint32_t acc = (written >> g) & 1u;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
@@ -558,133 +649,203 @@ __global__ void __launch_bounds__(256, 1) k_square_tc(TcArgs a) {
             written |= 1u << g;
             ++nprod;
           }
+          if (!ok) break;
         }
         mma_commit(&empty[s]);
+        if (!ok) break;
       }
-      if (!ok) status[0] = 1;
-      status[3] = (int32_t)written;
-      // slice-pair products issued (each 2 MMAs of 128 x 128 x 16)
-      if (a.err && nprod) atomicAdd(reinterpret_cast<unsigned long long*>(a.err + 2), nprod);
-      mma_commit(accb);   // arrives once every MMA issued above has completed
+      if (!ok || done) break;
+      // the slot's previous tile (it - 2) has been released by now: the producer
+      // started this tile only after the epilogue finished that one
+      while (released < it - 1 && ok) ok = reclaim();
+      if (b) pend1 = used;
+      else pend0 = used;
+      gmap[b] = written | (gblk << 8);
+      mma_commit(&acc_full[b]);    // arrives once every MMA of the tile has completed
+      mbar_arrive(&acc_full[b]);   // release: group map visible to the epilogue
     }
-    __syncwarp();
-    __syncthreads();
-
-    // ---------------- epilogue (all 8 warps)
-    step_base += status[1];
-    const uint32_t written = (uint32_t)status[3];
-    // block-uniform outcome of the bounded wait (a late completion must not split the CTA)
-    const bool acc_ok = !__syncthreads_or(!mbar_wait(accb, tile_iter & 1u) || status[0] != 0);
-    if (!acc_ok) alive = false;
-    tc_fence_after();
-    const int quarter = warp & 3;          // TMEM lanes 32*quarter .. +31
-    const int half = warp >> 2;            // columns 64*half .. +63
-    const int Ia = I0 + quarter;           // tile row of this thread
-    const int r = lane;                    // row inside the tile
-    const int64_t gi = (int64_t)Ia * TB + r;
-    for (int hb = 0; hb < 2 && alive; ++hb) {   // two tiles per half: b = 2*half + hb
-      const int b = 2 * half + hb;
-      const int Jb = J0 + b;
-      const bool valid = Ia < a.nb && Jb < a.nb && Ia <= Jb;
-      // output tile index (if present in the output pattern)
-      int oidx = -1;
-      if (valid) {
-        const uint32_t* ob = a.obits + (int64_t)Ia * a.words;
-        const uint32_t mo = ob[Jb >> 5];
-        if ((mo >> (Jb & 31)) & 1u) {
-          int pos = a.orowptr[Ia];
-          for (int w = 0; w < (Jb >> 5); ++w) pos += __popc(ob[w]);
-          oidx = pos + __popc(mo & ((1u << (Jb & 31)) - 1u));
+    if (!ok) status[0] = 1;
+    // slice-pair products issued (each 2 MMAs of 128 x 128 x 16)
+    if (a.err && nprod) atomicAdd(reinterpret_cast<unsigned long long*>(a.err + 2), nprod);
+    mma_commit(drain);
+    if (!mbar_wait(drain, 0)) status[0] = 1;
+  } else if (warp >= 2) {
+    // ---------------- epilogue (warps 2-9, two per SM sub-partition: warp w
+    // reads TMEM lanes 32 (w % 4)..+31 = tile row I0 + w % 4, lane = row inside
+    // the tile; warps 2-5 take column tiles 0-1, warps 6-9 column tiles 2-3).
+    // Phase 1 moves the exact fixed-point sums to the CTA's scratch and returns
+    // the TMEM blocks, so the next tile's products run during phase 2, the FP64
+    // arithmetic.
+    const int quarter = warp & 3;
+    const int bt0 = 2 * ((warp - 2) >> 2);
+    const int r = lane;
+    const double su = Cfg::UNIT * a.scale;   // S = fx * su, su a power of two
+    const int lsu = ilogb(su);
+    // X_new = c0 I + c1 X~ + c2 S.  Without acceleration (alpha = 1) the two
+    // polynomials need fewer FP64 operations, with the same results:
+    //   x^2 (c0 = c1 = 0, c2 = 1): S itself;  2x - x^2 (c0 = 0, c1 = 2, c2 = -1): 2 z - S.
+    const int form = (a.c0 == 0.0 && a.c1 == 0.0 && a.c2 == 1.0) ? 1
+                   : (a.c0 == 0.0 && a.c1 == 2.0 && a.c2 == -1.0) ? 2 : 0;
+    // index of tile (row, col) in a pattern given by row bitmaps and row
+    // offsets, -1 if absent; the lanes share the popcount of the row's words
+    auto find = [&](const uint32_t* bits, const int32_t* rowptr, int row, int col) -> int {
+      const uint32_t* rb = bits + (int64_t)row * a.words;
+      const int wc = col >> 5;
+      const uint32_t m = rb[wc];
+      if (!((m >> (col & 31)) & 1u)) return -1;
+      int cnt = 0;
+      for (int w = lane; w < wc; w += 32) cnt += __popc(rb[w]);
+      cnt = __reduce_add_sync(FULLW, cnt);
+      return rowptr[row] + cnt + __popc(m & ((1u << (col & 31)) - 1u));
+    };
+    for (int it = 0;; ++it) {
+      const int b = it & 1;
+      const uint32_t par = ((uint32_t)it >> 1) & 1u;
+      bool good = true;
+      if (lane == 0) good = mbar_wait(&tile_full[b], par);
+      good = __shfl_sync(FULLW, good ? 1 : 0, 0) != 0;
+      if (!good) { if (lane == 0) status[0] = 1; break; }
+      __syncwarp();
+      const int idx = tslot[b];
+      if (idx < 0) break;
+      if (lane == 0) good = mbar_wait(&acc_full[b], par);
+      good = __shfl_sync(FULLW, good ? 1 : 0, 0) != 0;
+      if (!good) { if (lane == 0) status[0] = 1; break; }
+      __syncwarp();
+      tc_fence_after();
+      const uint32_t gm = gmap[b];
+      const uint32_t written = gm & 0xFu;
+      const int stile = a.list[idx];
+      const int R = stile / a.nsr, C = stile % a.nsr;
+      const int I0 = 4 * R, J0 = 4 * C;
+      const int Ia = I0 + quarter;           // tile row of this thread
+      const int64_t gi = (int64_t)Ia * TB + r;
+      long long* scr = a.scratch + ((int64_t)blockIdx.x * 2 + b) * (ST * ST) + (int64_t)(quarter * 32 + r) * ST;
+      // phase 1: output tile index of each column tile; TMEM -> scratch
+      int oidx[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int Jb = J0 + bt0 + h;
+        oidx[h] = (Ia < a.nb && Jb < a.nb && Ia <= Jb) ? find(a.obits, a.orowptr, Ia, Jb) : -1;
+      }
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int bt = bt0 + h;
+        if (oidx[h] < 0) continue;      // warp-uniform
+#pragma unroll
+        for (int ch = 0; ch < 2; ++ch) {
+          const int col0 = bt * 32 + ch * 16;
+          long long fx[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) fx[i] = 0;
+#pragma unroll
+          for (int gg = 0; gg < K; ++gg) {
+            if ((written >> gg) & 1u) {   // warp-uniform: groups no product reached are zero
+              float g[16];
+              const uint32_t blk = (gm >> (8 + 2 * gg)) & 3u;
+              tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + blk * ST + (uint32_t)col0, g);
+#pragma unroll
+              for (int i = 0; i < 16; ++i) fx[i] += f32_int_to_ll(g[i]) * (1ll << (11 * (K - 1 - gg)));
+            }
+          }
+          longlong2* sp = reinterpret_cast<longlong2*>(scr + col0);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) sp[i] = make_longlong2(fx[2 * i], fx[2 * i + 1]);
         }
       }
-      // Z_IJ (X~_IJ in the forward step; absent -> 0)
-      const double* Zt = nullptr;
-      if (oidx >= 0) {
-        const uint32_t* bz = a.zbits + (int64_t)Ia * a.words;
-        const uint32_t mz = bz[Jb >> 5];
-        if ((mz >> (Jb & 31)) & 1u) {
-          int pos = a.zrowptr[Ia];
-          for (int w = 0; w < (Jb >> 5); ++w) pos += __popc(bz[w]);
-          pos += __popc(mz & ((1u << (Jb & 31)) - 1u));
-          const int64_t zi = (int64_t)(a.zref[pos] & ~REF_T);
+      // this warp's TMEM reads are complete: release its share of the blocks
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) {
+        __threadfence_block();
+        atomicAdd(tfree, 1u);
+      }
+      // phase 2: X_new, per-tile ||X~ - S||^2, ||X_new||^2 and traces
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int bt = bt0 + h;
+        const int Jb = J0 + bt;
+        const int oi = oidx[h];
+        if (oi < 0) continue;
+        // Z_IJ (X~_IJ in the forward step; absent -> 0)
+        const double* Zt = nullptr;
+        const int zp = find(a.zbits, a.zrowptr, Ia, Jb);
+        if (zp >= 0) {
+          const int64_t zi = (int64_t)(a.zref[zp] & ~REF_T);
           Zt = a.zpool + (int64_t)(a.zslot ? a.zslot[zi] : zi) * TE;
         }
-      }
-      double e2 = 0.0, trS = 0.0, trX = 0.0, n2 = 0.0;
-      // S = fx * UNIT * scale with fx the exact fixed-point sum of the groups; the
-      // unit is folded into the coefficients: xn = c0 [diag] + c1 z + (c2 su) fx
-      const double su = Cfg::UNIT * a.scale;
-      const double c2u = a.c2 * su;
-      for (int ch = 0; ch < 2; ++ch) {     // 16 columns per chunk
-        const int col0 = b * 32 + ch * 16;
-        double zv[16];
+        double trS = 0.0, trX = 0.0, n2 = 0.0;
+        // ||X~ - S||^2 only steers the stopping test: FP64 differences, squared
+        // and summed in FP32
+        float e2f = 0.0f;
+        double* O = a.opool + (int64_t)oi * TE;
+        for (int ch = 0; ch < 2; ++ch) {     // 16 columns per chunk
+          const int col0 = bt * 32 + ch * 16;
+          double zv[16];
 #pragma unroll
-        for (int i = 0; i < 16; ++i) zv[i] = 0.0;
-        if (oidx >= 0 && Zt) {
-          const double2* zp = reinterpret_cast<const double2*>(Zt + r * TB + ch * 16);
+          for (int i = 0; i < 16; ++i) zv[i] = 0.0;
+          if (Zt) {
+            const double2* zp = reinterpret_cast<const double2*>(Zt + r * TB + ch * 16);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const double2 t2 = zp[i];
+              zv[2 * i] = t2.x;
+              zv[2 * i + 1] = t2.y;
+            }
+          }
+          long long fx[16];
+          const longlong2* sp = reinterpret_cast<const longlong2*>(scr + col0);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const double2 t2 = zp[i];
-            zv[2 * i] = t2.x;
-            zv[2 * i + 1] = t2.y;
+            const longlong2 t2 = sp[i];
+            fx[2 * i] = t2.x;
+            fx[2 * i + 1] = t2.y;
           }
-        }
-        float g[K][16];
+          double out[16];
 #pragma unroll
-        for (int gg = 0; gg < K; ++gg) {
-          if ((written >> gg) & 1u) {   // block-uniform: groups no product reached are zero
-            tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)(gg * ST + col0), g[gg]);
-          } else {
-#pragma unroll
-            for (int i = 0; i < 16; ++i) g[gg][i] = 0.0f;
+          for (int i = 0; i < 16; ++i) {
+            const int c = ch * 16 + i;
+            const int64_t gj = (int64_t)Jb * TB + c;
+            const bool inside = gi < a.n && gj < a.n;
+            const double fxd = inside ? (double)fx[i] : 0.0;
+            const double z = inside ? zv[i] : 0.0;
+            const bool dg = inside && gi == gj;
+            const double S = int_times_pow2(fxd, lsu);       // fx * su
+            double xn;
+            // c2 S = (c2 su) fx exactly (su is a power of two)
+            if (form == 1) xn = S;
+            else if (form == 2) xn = twice(z) - S;
+            else xn = fma(a.c2, S, fma(a.c1, z, dg ? a.c0 : 0.0));
+            out[i] = xn;
+            const float df = f64_hi_to_f32(z - S);
+            e2f = fmaf(df, df, e2f);
+            n2 = fma(xn, xn, n2);
+            if (dg) { trS += S; trX += z; }
           }
+          double2* op = reinterpret_cast<double2*>(O + r * TB + ch * 16);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) op[i] = make_double2(out[2 * i], out[2 * i + 1]);
         }
-        if (oidx < 0) continue;
-        double* O = a.opool + (int64_t)oidx * TE;
-        double out[16];
-#pragma unroll
-        for (int i = 0; i < 16; ++i) {
-          const int c = ch * 16 + i;
-          const int64_t gj = (int64_t)Jb * TB + c;
-          const bool inside = gi < a.n && gj < a.n;
-          long long fx = 0;
-#pragma unroll
-          for (int gg = 0; gg < K; ++gg) fx += f32_int_to_ll(g[gg][i]) * (1ll << (11 * (K - 1 - gg)));
-          const double fxd = inside ? (double)fx : 0.0;
-          const double z = inside ? zv[i] : 0.0;
-          const bool dg = inside && gi == gj;
-          const double xn = inside ? fma(c2u, fxd, fma(a.c1, z, dg ? a.c0 : 0.0)) : 0.0;
-          out[i] = xn;
-          const double d = fma(fxd, -su, z);
-          e2 = fma(d, d, e2);
-          n2 = fma(xn, xn, n2);
-          if (dg) { trS += fxd * su; trX += z; }
+        // warp reductions (the tile's 32 rows are this warp's 32 lanes)
+        double e2 = (double)e2f;
+        for (int o = 16; o > 0; o >>= 1) {
+          e2 += __shfl_xor_sync(FULLW, e2, o);
+          n2 += __shfl_xor_sync(FULLW, n2, o);
+          trS += __shfl_xor_sync(FULLW, trS, o);
+          trX += __shfl_xor_sync(FULLW, trX, o);
         }
-        double2* op = reinterpret_cast<double2*>(O + r * TB + ch * 16);
-#pragma unroll
-        for (int i = 0; i < 8; ++i) op[i] = make_double2(out[2 * i], out[2 * i + 1]);
+        if (lane == 0) {
+          const bool diag = Ia == Jb;
+          a.part.e2[oi] = (diag ? 1.0 : 2.0) * e2;
+          a.part.n2[oi] = n2;
+          a.part.trS[oi] = diag ? trS : 0.0;
+          a.part.trX[oi] = diag ? trX : 0.0;
+          a.part.ktiles[oi] = kcount[b * 16 + quarter * 4 + bt];
+        }
       }
-      // warp reductions (the tile's 32 rows are this warp's 32 lanes)
-      for (int o = 16; o > 0; o >>= 1) {
-        e2 += __shfl_xor_sync(0xffffffffu, e2, o);
-        n2 += __shfl_xor_sync(0xffffffffu, n2, o);
-        trS += __shfl_xor_sync(0xffffffffu, trS, o);
-        trX += __shfl_xor_sync(0xffffffffu, trX, o);
-      }
-      if (lane == 0 && oidx >= 0) {
-        const bool diag = Ia == Jb;
-        a.part.e2[oidx] = (diag ? 1.0 : 2.0) * e2;
-        a.part.n2[oidx] = n2;
-        a.part.trS[oidx] = diag ? trS : 0.0;
-        a.part.trX[oidx] = diag ? trX : 0.0;
-        a.part.ktiles[oidx] = kcount[quarter * 4 + b];
-      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&tile_empty[b]);
     }
-    if (threadIdx.x == 0 && a.err && !acc_ok) atomicOr(a.err, 1);
-    // TMEM reads of this tile are complete before the next tile's MMAs start
-    tc_fence_before();
-    __syncthreads();
-    tc_fence_after();
   }
   __syncthreads();
   if (warp == 1) {
@@ -823,20 +984,20 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   a.obits = L.obits; a.orowptr = L.orowptr; a.list = L.list; a.count = L.count; a.work = L.work;
   a.opool = L.opool;
   a.part = L.part; a.c0 = L.c0; a.c1 = L.c1; a.c2 = L.c2; a.scale = L.scale; a.n = L.n; a.nb = L.nb;
-  a.words = L.words; a.nsr = L.nsr; a.err = L.err;
+  a.words = L.words; a.nsr = L.nsr; a.err = L.err; a.scratch = static_cast<long long*>(L.scratch);
   cudaError_t e = cudaSuccess;
   switch (L.k) {
     case 2:
       e = cudaFuncSetAttribute(k_square_tc<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<2>::SMEM);
-      if (e == cudaSuccess) { ++g_launches; k_square_tc<2><<<(unsigned)L.nsuper, 256, TcCfg<2>::SMEM, st>>>(a); }
+      if (e == cudaSuccess) { ++g_launches; k_square_tc<2><<<(unsigned)L.nsuper, TC_THREADS, TcCfg<2>::SMEM, st>>>(a); }
       break;
     case 3:
       e = cudaFuncSetAttribute(k_square_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<3>::SMEM);
-      if (e == cudaSuccess) { ++g_launches; k_square_tc<3><<<(unsigned)L.nsuper, 256, TcCfg<3>::SMEM, st>>>(a); }
+      if (e == cudaSuccess) { ++g_launches; k_square_tc<3><<<(unsigned)L.nsuper, TC_THREADS, TcCfg<3>::SMEM, st>>>(a); }
       break;
     default:
       e = cudaFuncSetAttribute(k_square_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<4>::SMEM);
-      if (e == cudaSuccess) { ++g_launches; k_square_tc<4><<<(unsigned)L.nsuper, 256, TcCfg<4>::SMEM, st>>>(a); }
+      if (e == cudaSuccess) { ++g_launches; k_square_tc<4><<<(unsigned)L.nsuper, TC_THREADS, TcCfg<4>::SMEM, st>>>(a); }
       break;
   }
   if (e != cudaSuccess) return e;

@@ -32,12 +32,14 @@ def test_split16_k4_meets_tolerance(key):
 
 
 def test_split16_first_square_matches_fp64_closely():
-    # one step only: e_0, t_0 come from S = X~_0^2; slices on a 2^-43 grid
+    # one step only: e_0, t_0 come from S = X~_0^2; slices on a 2^-43 grid.  The
+    # tensor path sums ||X~ - S||^2 (which only steers the stopping test) in FP32
+    # from FP64 differences; t uses FP64 traces.
     c = make_config("2s")
     a = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], n_max_cap=1)
     b = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], n_max_cap=1, precision="split16", slices=4)
     ea, eb = a["stats"]["e"], b["stats"]["e"]
-    np.testing.assert_allclose(eb, ea, rtol=1e-9)
+    np.testing.assert_allclose(eb, ea, rtol=1e-5)
     np.testing.assert_allclose(b["stats"]["t"], a["stats"]["t"], rtol=1e-9)
     # 5.9M elements, each within ~1e-12 (2^-44 grid, FP32-exact groups)
     assert np.linalg.norm(a["D"] - b["D"]) < 1e-8
