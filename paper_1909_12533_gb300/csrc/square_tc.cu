@@ -196,7 +196,7 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 template <int K>
 __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ index, const int32_t* __restrict__ slot,
                                                        const double* __restrict__ pool, __half* data,
-                                                       uint8_t* head, int32_t* err, double inv_scale) {
+                                                       uint8_t* head, int32_t* err, int lscale) {
   __shared__ __align__(16) __half sm[K * 4 * TE];
   __shared__ uint32_t wnz[8];
   const int64_t e = blockIdx.x;
@@ -214,12 +214,26 @@ __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ 
     for (int i = threadIdx.x; i < TE; i += blockDim.x) {
       // stored element (i / 32, i % 32) is element (r, c) of the panel's tile
       const int r = tr ? (i & 31) : (i >> 5), c = tr ? (i >> 5) : (i & 31);
-      double x = present ? src[i] * inv_scale : 0.0;
-      if (!(fabs(x) < 2.0)) {
+      // v = x / scale * 2^FIN rounded to the nearest integer (ties to even),
+      // from the bits of x = m 2^(ex - 1075): v = m >> sh on the integer pipes
+      const long long xb = present ? __double_as_longlong(src[i]) : 0ll;
+      const int ex = (int)((xb >> 52) & 0x7FF);
+      long long v = 0;
+      if (ex - lscale >= 1024) {           // |x / scale| >= 2, inf or NaN: flagged, clamped
         if (err) atomicOr(err, 4);
-        x = fmin(fmax(x, -1.999), 1.999);
+        v = (1ll << (FIN + 1)) - 1;
+        if (xb < 0) v = -v;
+      } else if (ex != 0) {
+        const unsigned long long m = ((unsigned long long)xb & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+        const int sh = 1075 + lscale - FIN - ex;   // >= 9 here
+        unsigned long long q = 0;
+        if (sh < 64) {
+          q = m >> sh;
+          const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
+          if (rem > half || (rem == half && (q & 1ull))) ++q;
+        }
+        v = xb < 0 ? -(long long)q : (long long)q;
       }
-      long long v = __double2ll_rn(x * (double)(1ll << FIN));
       int T[K];
 #pragma unroll
       for (int s = 0; s < K - 1; ++s) {
@@ -866,12 +880,12 @@ cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32
   if (nrec == 0) return cudaSuccess;
   const uint4* ix = reinterpret_cast<const uint4*>(index);
   __half* d = static_cast<__half*>(data);
-  const double inv = 1.0 / scale;   // scale is a power of two: exact
+  const int ls = ilogb(scale);   // scale is a power of two
   const unsigned g = (unsigned)nrec;
   ++g_launches;
-  if (k == 2) k_panel_slices<2><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, inv);
-  else if (k == 3) k_panel_slices<3><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, inv);
-  else k_panel_slices<4><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, inv);
+  if (k == 2) k_panel_slices<2><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls);
+  else if (k == 3) k_panel_slices<3><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls);
+  else k_panel_slices<4><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls);
   return cudaGetLastError();
 }
 
