@@ -83,7 +83,10 @@ typedef struct {
 } sp2_bsr;
 
 /* Optional device allocator.  alloc returns NULL on failure (-> SP2_ERR_OOM).
- * NULL allocator = cudaMallocAsync / cudaFreeAsync on the context's stream. */
+ * NULL allocator = stream-ordered allocation (cudaMallocFromPoolAsync /
+ * cudaFreeAsync on the context's stream) from a memory pool the library keeps
+ * per device: memory a destroyed context freed is reused by the next context
+ * without going back to the driver; sp2_release_memory() returns it. */
 typedef struct {
   void* (*alloc)(size_t bytes, void* user);
   void (*free)(void* ptr, void* user);
@@ -215,6 +218,12 @@ int sp2_truncate_noalloc(const int32_t* brow, const int32_t* bcol, const double*
 int sp2_get_stats(const sp2_ctx* ctx, sp2_stats* stats);
 void sp2_destroy(sp2_ctx* ctx);
 const char* sp2_strerror(int code);
+
+/* Not in the paper: hand the device memory cached by the library's memory
+ * pools (memory of destroyed contexts, kept for reuse) back to the driver,
+ * after the work queued on every device has finished.  Contexts alive keep
+ * their memory.  Errors: CUDA. */
+int sp2_release_memory(void);
 
 #ifdef __cplusplus
 }

@@ -75,6 +75,7 @@ _SIGS = [
     ("sp2_get_stats", c_int32, [c_void_p, POINTER(sp2_stats)]),
     ("sp2_destroy", None, [c_void_p]),
     ("sp2_strerror", ctypes.c_char_p, [c_int32]),
+    ("sp2_release_memory", c_int32, []),
 ]
 
 _LIB = None
@@ -108,6 +109,13 @@ class SP2Error(RuntimeError):
 
 def sp2_strerror(code: int) -> str:
     return load().sp2_strerror(code).decode()
+
+
+def sp2_release_memory() -> None:
+    """Return the device memory the library's pools keep for reuse."""
+    rc = load().sp2_release_memory()
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_release_memory")
 
 
 def sp2_default_params(**overrides) -> sp2_params:

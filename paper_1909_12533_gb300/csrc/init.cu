@@ -8,28 +8,44 @@ namespace {
 
 // One warp per tile row I, lane r = row inside the tile.  Row i's radius
 // sum_{j != i} |F_ij| is accumulated sequentially over the row's tiles in
-// ascending K, so the result does not depend on scheduling.
-__global__ void k_gershgorin(const int32_t* __restrict__ frowptr, const int32_t* __restrict__ fcol,
-                             const uint32_t* __restrict__ fref, const double* __restrict__ pool, int nb, int64_t n,
-                             double* rowlo, double* rowhi) {
-  const int I = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+// ascending K, so the result does not depend on scheduling.  Each tile is
+// read with coalesced loads and staged (in the orientation row I needs) in
+// shared memory, rows padded to 33 doubles.
+constexpr int GER_WARPS = 4;
+
+__global__ void __launch_bounds__(32 * GER_WARPS) k_gershgorin(const int32_t* __restrict__ frowptr,
+                                                               const int32_t* __restrict__ fcol,
+                                                               const uint32_t* __restrict__ fref,
+                                                               const double* __restrict__ pool, int nb, int64_t n,
+                                                               double* rowlo, double* rowhi) {
+  __shared__ double tile[GER_WARPS][TB][TB + 1];
+  const int wid = threadIdx.x >> 5;
+  const int I = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
   const int r = threadIdx.x & 31;
-  if (I >= nb) return;
+  if (I >= nb) return;   // whole warps leave together
   const int64_t gi = (int64_t)I * TB + r;
-  if (gi >= n) return;
+  double (*ts)[TB + 1] = tile[wid];
   double d = 0.0, s = 0.0;
   for (int e = frowptr[I]; e < frowptr[I + 1]; ++e) {
     const int K = fcol[e];
     const uint32_t rf = fref[e];
     const double* T = pool + (int64_t)(rf & ~REF_T) * TE;
     const bool tr = (rf & REF_T) != 0;
+    __syncwarp();
+    for (int i = 0; i < TB; ++i) {
+      const double v = T[i * TB + r];      // stored row i, column r
+      if (tr) ts[r][i] = v;
+      else ts[i][r] = v;
+    }
+    __syncwarp();
     for (int c = 0; c < TB; ++c) {
       const int64_t gk = (int64_t)K * TB + c;
       if (gk >= n) break;
-      const double v = tr ? T[c * TB + r] : T[r * TB + c];
+      const double v = ts[r][c];
       if (gk == gi) d = v; else s += fabs(v);
     }
   }
+  if (gi >= n) return;
   rowlo[gi] = d - s;
   rowhi[gi] = d + s;
 }
@@ -94,7 +110,9 @@ __global__ void __launch_bounds__(256) k_x0(const int32_t* __restrict__ brow, co
 cudaError_t launch_gershgorin(const FullPattern& fp, const double* pool, int nb, int64_t n, double* rowlo,
                               double* rowhi, cudaStream_t st) {
   const int64_t thr = (int64_t)nb * 32;
-  { ++g_launches; k_gershgorin<<<(unsigned)((thr + 255) / 256), 256, 0, st>>>(fp.rowptr, fp.col, fp.ref, pool, nb, n, rowlo, rowhi); }
+  const int bs = 32 * GER_WARPS;
+  ++g_launches;
+  k_gershgorin<<<(unsigned)((thr + bs - 1) / bs), bs, 0, st>>>(fp.rowptr, fp.col, fp.ref, pool, nb, n, rowlo, rowhi);
   return cudaGetLastError();
 }
 

@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 #include <algorithm>
+#include <mutex>
 
 #include "sp2_internal.h"
 
@@ -190,15 +191,48 @@ void estimates(const Schedule& s, const std::vector<double>& e, const std::vecto
 }
 
 // ------------------------------------------------------------------ memory
+// One stream-ordered memory pool per device, kept for the life of the process
+// with no release threshold: a context created after another was destroyed
+// takes its memory from the pool instead of the driver.
+constexpr int kMaxDevices = 64;
+std::mutex g_pool_mu;
+cudaMemPool_t g_pool[kMaxDevices] = {};
+
+cudaMemPool_t device_pool() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  if (!g_pool[dev]) {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = dev;
+    cudaMemPool_t p = nullptr;
+    if (cudaMemPoolCreate(&p, &props) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep);
+    g_pool[dev] = p;
+  }
+  return g_pool[dev];
+}
+
 struct Alloc {
   sp2_allocator a{};
   bool custom = false;
   cudaStream_t st = nullptr;
+  cudaMemPool_t pool = nullptr;
   void* get(size_t bytes) {
     if (bytes == 0) bytes = 256;
     if (custom) return a.alloc(bytes, a.user);
     void* p = nullptr;
-    if (cudaMallocAsync(&p, bytes, st) != cudaSuccess) {
+    const cudaError_t e = pool ? cudaMallocFromPoolAsync(&p, bytes, pool, st) : cudaMallocAsync(&p, bytes, st);
+    if (e != cudaSuccess) {
       cudaGetLastError();
       return nullptr;
     }
@@ -630,6 +664,29 @@ int sp2_default_params(sp2_params* p) {
   return SP2_OK;
 }
 
+int sp2_release_memory(void) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  int prev = 0;
+  if (cudaGetDevice(&prev) != cudaSuccess) {
+    cudaGetLastError();
+    return SP2_ERR_CUDA;
+  }
+  int rc = SP2_OK;
+  for (int d = 0; d < kMaxDevices; ++d) {
+    if (!g_pool[d]) continue;
+    if (cudaSetDevice(d) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemPoolTrimTo(g_pool[d], 0) != cudaSuccess) {
+      cudaGetLastError();
+      rc = SP2_ERR_CUDA;
+    }
+  }
+  if (cudaSetDevice(prev) != cudaSuccess) {
+    cudaGetLastError();
+    rc = SP2_ERR_CUDA;
+  }
+  return rc;
+}
+
 const char* sp2_strerror(int code) {
   switch (code) {
     case SP2_OK: return "ok";
@@ -678,6 +735,8 @@ int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, d
   if (alloc) {
     c->al.a = *alloc;
     c->al.custom = true;
+  } else {
+    c->al.pool = device_pool();
   }
   c->prm = prm;
   c->n = F->n;

@@ -377,7 +377,7 @@ constexpr uint32_t HEAD_NONE = 0x07u;   // header of a K index outside the step 
 
 template <int K>
 struct TcCfg {
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 96 * 16;
   // unit of the finest group, 2^-(11 (k + 1) - 2)
   static constexpr double UNIT = 1.0 / (double)(1ull << (11 * (K + 1) - 2));
 };
@@ -400,6 +400,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   uint32_t* gmap = reinterpret_cast<uint32_t*>(kcount + 32);       // [2] groups written, block of each
   uint32_t* rec = gmap + 2;                                         // [STAGES] sub-step records
   int32_t* status = reinterpret_cast<int32_t*>(rec + STAGES);      // [0] a wait timed out
+  uint4* ulist = reinterpret_cast<uint4*>(smem_raw + STAGES * STAGE_BYTES + 1024);   // [96] sub-steps of a batch
   uint32_t* tfree = reinterpret_cast<uint32_t*>(status + 1);       // TMEM blocks released (warps x tiles)
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -436,39 +437,42 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   // i + 2 are being loaded and multiplied.  Tiles pass through two slots.
   if (warp == 0) {
     // ---------------- producer warp.  The record headers of 32 K steps are
-    // fetched at a time (lane j: step j), one batch ahead of their use;
-    // lanes 0-3 copy the units A0, A1, B0, B1 of a sub-step.
+    // fetched at a time (lane j: step j), one batch ahead of their use; the
+    // lanes turn them into the batch's list of sub-steps in shared memory, and
+    // lanes 0-3 issue the sub-steps, lane u copying unit u (A0, A1, B0, B1) and
+    // lane 0 writing the stage record and arming its barrier.  Every lane keeps
+    // its own copy of the stage counter; no warp votes per sub-step.
     int step = 0;
     bool ok = true;
-    // one sub-step: wait for the stage, write the record, arm the barrier,
-    // start the copies (srcA / srcB: the K step's A and B panel records)
+    // lanes 0-3: one sub-step (srcA / srcB: the K step's A and B panel records)
     auto emit = [&](uint32_t rv, const __half* srcA, const __half* srcB) -> bool {
       const int s = step % STAGES;
       const uint32_t par = ((step / STAGES) & 1) ^ 1;
-      int good = 1;
-      if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
-      good = __shfl_sync(FULLW, good, 0);
-      if (!good) {
-        if (lane == 0) status[0] = 1;
+      ++step;
+      if (!mbar_wait(&empty[s], par)) {
+        status[0] = 1;
         return false;
       }
-      bool ld = false;
-      const __half* src = nullptr;
-      if (!(rv & (REC_END | REC_LAST)) && lane < 4) {
-        const uint32_t mask = (rv >> 8) & 0xFu;
-        const uint32_t umask = lane == 0 ? 0x3u : lane == 1 ? 0xCu : lane == 2 ? 0x5u : 0xAu;
-        ld = (mask & umask) != 0;
-        src = (lane < 2 ? srcA : srcB) + (int64_t)((rv >> (2 * lane)) & 3u) * (UNIT_BYTES / 2);
-      }
-      const uint32_t lm = __ballot_sync(FULLW, ld);
+      const uint32_t mask = (rv & (REC_END | REC_LAST)) ? 0u : (rv >> 8) & 0xFu;
+      // units A0, A1, B0, B1 read by a product of the mask
+      const uint32_t use = ((mask & 0x3u) ? 1u : 0u) | ((mask & 0xCu) ? 2u : 0u) | ((mask & 0x5u) ? 4u : 0u) |
+                           ((mask & 0xAu) ? 8u : 0u);
       if (lane == 0) {
         rec[s] = rv;
-        mbar_expect_tx(&full[s], (uint32_t)__popc(lm) * UNIT_BYTES);
+        mbar_expect_tx(&full[s], (uint32_t)__popc(use) * UNIT_BYTES);
       }
-      __syncwarp();
-      if (ld) bulk_g2s(stage_base + s * STAGE_BYTES + lane * UNIT_BYTES, src, UNIT_BYTES, &full[s]);
-      ++step;
+      if ((use >> lane) & 1u)
+        bulk_g2s(stage_base + s * STAGE_BYTES + lane * UNIT_BYTES,
+                 (lane < 2 ? srcA : srcB) + (int64_t)((rv >> (2 * lane)) & 3u) * (UNIT_BYTES / 2), UNIT_BYTES,
+                 &full[s]);
       return true;
+    };
+    // all lanes: a control sub-step (no data), issued by lane 0
+    auto emit_ctl = [&](uint32_t rv) -> bool {
+      bool r = true;
+      if (lane == 0) r = emit(rv, nullptr, nullptr);
+      else ++step;
+      return __shfl_sync(FULLW, r ? 1 : 0, 0) != 0;
     };
     for (int it = 0; ok; ++it) {
       const int b = it & 1;
@@ -489,7 +493,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           tslot[b] = -1;
           mbar_arrive(&tile_full[b]);
         }
-        emit(REC_LAST, nullptr, nullptr);
+        emit_ctl(REC_LAST);
         break;
       }
       const int stile = a.list[idx];
@@ -561,29 +565,52 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
               const int c16 = __popc(__ballot_sync(FULLW, (pa4 >> (t >> 2)) & (pb4 >> (t & 3)) & 1u));
               if (lane == t) kc += c16;
             }
-            // only K steps with at least one slice pair s + t <= K - 1
+            // sub-steps of this lane's K step: pairs s >= fa, t >= fb, s + t <= K - 1,
+            // two A and two B slices each (at most three for K = 4)
             const int fa = (int)(ha & 7u), fb = (int)(hb & 7u);
-            uint32_t act = __ballot_sync(FULLW, fa + fb <= K - 1);
-            while (act && ok) {
-              const int j = __ffs(act) - 1;
-              act &= act - 1;
-              const int fA = __shfl_sync(FULLW, fa, j), fB = __shfl_sync(FULLW, fb, j);
-              const int eA = __shfl_sync(FULLW, ea, j), eB = __shfl_sync(FULLW, eb, j);
-              const __half* srcA = opA.data + (int64_t)eA * (K * UNIT_BYTES / 2);
-              const __half* srcB = opB.data + (int64_t)eB * (K * UNIT_BYTES / 2);
-              // pairs s >= fA, t >= fB, s + t <= K - 1, two A and two B slices per sub-step
-              for (int a0 = fA; a0 + fB <= K - 1 && ok; a0 += 2) {
-                for (int b0 = fB; a0 + b0 <= K - 1 && ok; b0 += 2) {
-                  uint32_t mask = 0;
-                  for (int i = 0; i < 2; ++i)
-                    for (int jj = 0; jj < 2; ++jj)
-                      if (a0 + i + b0 + jj <= K - 1) mask |= 1u << (2 * i + jj);
-                  const uint32_t rv = (uint32_t)a0 | ((uint32_t)min(a0 + 1, K - 1) << 2) | ((uint32_t)b0 << 4) |
-                                      ((uint32_t)min(b0 + 1, K - 1) << 6) | (mask << 8);
-                  ok = emit(rv, srcA, srcB);
-                }
+            uint32_t rv0 = 0u, rv1 = 0u, rv2 = 0u;
+            int ns = 0;
+            for (int a0 = fa; a0 + fb <= K - 1; a0 += 2) {
+              for (int b0 = fb; a0 + b0 <= K - 1; b0 += 2) {
+                uint32_t mask = 0;
+                for (int i = 0; i < 2; ++i)
+                  for (int jj = 0; jj < 2; ++jj)
+                    if (a0 + i + b0 + jj <= K - 1) mask |= 1u << (2 * i + jj);
+                const uint32_t rv = (uint32_t)a0 | ((uint32_t)min(a0 + 1, K - 1) << 2) | ((uint32_t)b0 << 4) |
+                                    ((uint32_t)min(b0 + 1, K - 1) << 6) | (mask << 8);
+                if (ns == 0) rv0 = rv;
+                else if (ns == 1) rv1 = rv;
+                else rv2 = rv;
+                ++ns;
               }
             }
+            int soff = ns;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+              const int v = __shfl_up_sync(FULLW, soff, o);
+              if (lane >= o) soff += v;
+            }
+            const int nsub = __shfl_sync(FULLW, soff, 31);
+            soff -= ns;
+            if (ns > 0) ulist[soff] = make_uint4(rv0, (uint32_t)ea, (uint32_t)eb, 0u);
+            if (ns > 1) ulist[soff + 1] = make_uint4(rv1, (uint32_t)ea, (uint32_t)eb, 0u);
+            if (ns > 2) ulist[soff + 2] = make_uint4(rv2, (uint32_t)ea, (uint32_t)eb, 0u);
+            __syncwarp();
+            bool lok = true;
+            if (lane < 4) {
+              for (int u = 0; u < nsub; ++u) {
+                const uint4 en = ulist[u];
+                if (!emit(en.x, opA.data + (int64_t)en.y * (K * UNIT_BYTES / 2),
+                          opB.data + (int64_t)en.z * (K * UNIT_BYTES / 2))) {
+                  lok = false;
+                  break;
+                }
+              }
+            } else {
+              step += nsub;
+            }
+            ok = __all_sync(FULLW, lok);
+            __syncwarp();   // the list is rebuilt for the next batch
             ea = ea_n;
             eb = eb_n;
             ha = ha_n;
@@ -591,7 +618,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           }
         }
       }
-      if (ok) ok = emit(REC_END, nullptr, nullptr);
+      if (ok) ok = emit_ctl(REC_END);
       if (lane < 16) kcount[b * 16 + lane] = kc;
       if (lane == 0) tslot[b] = idx;
       __syncwarp();
