@@ -109,6 +109,10 @@ typedef struct {
   int32_t ckpt_every;      /* adjoint checkpoint interval k (X~_i kept for i % k == 0); default 8 */
   int32_t record_masks;    /* 1: keep per-iteration tile masks and FP64 checkpoints (needed by
                               sp2_backward; memory grows by one X~ per ckpt_every steps); default 0 */
+  double fp64_tail;        /* SPLIT16 with the idempotency stop: once e_j < fp64_tail, and in any case
+                              for the last four squares up to n_max + 1, the squares run in
+                              FP64, so the final idempotency steps reach FP64 accuracy;
+                              0 = never; default 1e-4                                   */
 } sp2_params;
 
 typedef struct {

@@ -290,6 +290,7 @@ struct sp2_ctx {
   Buf x_brow, x_bcol, x_slot, x_rowptr;      // index set 0 of X~
   Buf y_brow, y_bcol, y_slot, y_rowptr;      // index set 1 (the next X~ while the stop test is pending)
   int xset = 0;
+  int tail_from = 0;   // first iteration of the FP64 tail (0: none yet)
   Buf o_brow, o_bcol, o_slot, o_rowptr, o_bits;
   Buf pool[2];
   int cur = 0;
@@ -503,6 +504,11 @@ bool use_tc(const sp2_ctx* c, int i) {
   if (p.precision != SP2_PREC_SPLIT16) return false;
   if (i < p.mixed_from) return false;
   if (p.mixed_until > 0 && i > p.mixed_until) return false;
+  if (c->tail_from > 0 && i >= c->tail_from) return false;
+  // idempotency stop: the last four squares up to the iteration limit are FP64
+  // too (each pair of FP64 steps squares the tensor path's rounding left on
+  // both spectral sides)
+  if (p.stop == SP2_STOP_IDEMPOTENCY && p.fp64_tail > 0.0 && i >= c->sch.n_max - 2) return false;
   return true;
 }
 
@@ -661,6 +667,7 @@ int sp2_default_params(sp2_params* p) {
   p->mixed_until = 0;
   p->ckpt_every = 8;
   p->record_masks = 0;
+  p->fp64_tail = 1e-4;
   return SP2_OK;
 }
 
@@ -719,6 +726,7 @@ int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, d
   if (params) prm = *params;
   if (prm.mode != SP2_MODE_SP2 && prm.mode != SP2_MODE_SP2ACC) return SP2_ERR_INVALID_ARG;
   if (prm.stop != SP2_STOP_PARAMETERLESS && prm.stop != SP2_STOP_IDEMPOTENCY) return SP2_ERR_INVALID_ARG;
+  if (!(prm.fp64_tail >= 0.0) || !std::isfinite(prm.fp64_tail)) return SP2_ERR_INVALID_ARG;
   if (prm.trunc != SP2_TRUNC_FROBENIUS && prm.trunc != SP2_TRUNC_FROBINF) return SP2_ERR_INVALID_ARG;
   if (prm.trunc == SP2_TRUNC_FROBINF && (prm.frobinf_part < TB || prm.frobinf_part % TB)) return SP2_ERR_INVALID_ARG;
   if (prm.n_max_cap < 1 || prm.n_max_cap > SP2_MAX_ITER - 2) return SP2_ERR_INVALID_ARG;
@@ -843,6 +851,7 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
     c->cur = 0;
     truncate_into_X(c, c->F, c->p_n2.as<double>(), sch.tau[0]);
     S.nnzb_hist[0] = c->X.nnzb;
+    c->tail_from = 0;
     free_recs(c);
     record(c, 0);
     std::vector<double> ev, tv;
@@ -932,6 +941,10 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       S.e[j] = ej;
       S.t[j] = tj;
       S.prec_hist[j] = tc ? SP2_PREC_SPLIT16 : SP2_PREC_FP64;
+      // the final idempotency steps run in FP64 (SPLIT16 with the idempotency stop)
+      if (c->prm.stop == SP2_STOP_IDEMPOTENCY && c->prm.fp64_tail > 0.0 && ej < c->prm.fp64_tail &&
+          c->tail_from == 0)
+        c->tail_from = i + 1;
       bool stop = false;
       if (c->prm.stop == SP2_STOP_PARAMETERLESS) {
         stop = j >= std::max(sch.n_min, 2) && sch.p[j] != sch.p[j - 1] && ev[j] > C_STOP * (ev[j - 2] * ev[j - 2]);

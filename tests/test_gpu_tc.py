@@ -87,3 +87,22 @@ def test_split16_block_diagonal_sparse_supertiles():
     g = run_gpu(Fb, 170, -0.4, 0.4, 0.0, stop="idempotency", precision="split16", slices=4)
     assert _err(g, o) <= MIXED_TOL
     assert list(zip(g["brow"].tolist(), g["bcol"].tolist())) == sorted(o.kept[o.n])
+
+
+def test_split16_fp64_tail_reaches_idempotency_tolerance():
+    # dense N = 512, idempotency stop at 1e-12: the tensor path alone stalls near
+    # its rounding floor; the final steps in FP64 reach the tolerance
+    c = make_config(1)
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"])
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision="split16",
+                slices=4)
+    st = g["stats"]
+    assert g["code"] == 0 and st["converged"]
+    assert st["e"][st["n"]] < 1e-12
+    ph = st["prec_hist"]
+    assert ph[0] == 1 and ph[-1] == 0 and sorted(ph, reverse=True) == ph   # tensor cores first, FP64 tail
+    assert _err(g, o) <= MIXED_TOL
+    # fp64_tail = 0: every square on the tensor cores
+    g0 = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision="split16",
+                 slices=4, fp64_tail=0.0, n_max_cap=20)
+    assert all(p == 1 for p in g0["stats"]["prec_hist"])
