@@ -90,6 +90,30 @@ __device__ __forceinline__ unsigned long long now_ns() {
   return t;
 }
 
+// try_wait that lets the hardware suspend the thread for up to hint_ns (it
+// resumes when the phase completes): for waiters off the critical path, so
+// they do not take issue slots from the warps sharing their sub-partition.
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t parity, uint32_t hint_ns) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity), "r"(hint_ns)
+      : "memory");
+  return ok != 0;
+}
+
+// Bounded wait with suspension between polls: false on timeout.
+__device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  while (!mbar_try_wait_sleep(bar, parity, 20000u))
+    if (now_ns() - t0 > WAIT_NS) return false;
+  return true;
+}
+
 // Bounded wait: false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -478,7 +502,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       const int b = it & 1;
       // the slot's previous tile (it - 2) has left the epilogue
       int good = 1;
-      if (lane == 0) good = mbar_wait(&tile_empty[b], (((uint32_t)it >> 1) & 1u) ^ 1u) ? 1 : 0;
+      if (lane == 0) good = mbar_wait_sleep(&tile_empty[b], (((uint32_t)it >> 1) & 1u) ^ 1u) ? 1 : 0;
       good = __shfl_sync(FULLW, good, 0);
       if (!good) {
         if (lane == 0) status[0] = 1;
@@ -640,6 +664,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       const unsigned long long t0 = now_ns();
       while (*(volatile uint32_t*)tfree < (uint32_t)EPI_WARPS * (uint32_t)(released + 1)) {
         if (now_ns() - t0 > WAIT_NS) return false;
+        __nanosleep(100);
       }
       __threadfence_block();
       tc_fence_after();
@@ -743,13 +768,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       const int b = it & 1;
       const uint32_t par = ((uint32_t)it >> 1) & 1u;
       bool good = true;
-      if (lane == 0) good = mbar_wait(&tile_full[b], par);
+      if (lane == 0) good = mbar_wait_sleep(&tile_full[b], par);
       good = __shfl_sync(FULLW, good ? 1 : 0, 0) != 0;
       if (!good) { if (lane == 0) status[0] = 1; break; }
       __syncwarp();
       const int idx = tslot[b];
       if (idx < 0) break;
-      if (lane == 0) good = mbar_wait(&acc_full[b], par);
+      if (lane == 0) good = mbar_wait_sleep(&acc_full[b], par);
       good = __shfl_sync(FULLW, good ? 1 : 0, 0) != 0;
       if (!good) { if (lane == 0) status[0] = 1; break; }
       __syncwarp();
