@@ -49,6 +49,17 @@ WORKLOADS = {
 CPU_SAMPLE_KEY = "2s"
 PEAK_FP64_TFLOPS = 1.25   # GB300 FP64 nominal (no FP64 tensor path on this chip)
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, mean bytes per launch) of the
+# square kernel from one ncu capture of the default workload, keyed by the sha256 prefix of the
+# kernel source it was taken on; reported only while the source is unchanged
+# (profiles/k_square_tc_water24k.md has the command).
+SQUARE_TC_TRAFFIC = {("water24k", 4): ("16d97aa940846a03", 13.892e9)}
+
+
+def _source_hash(name: str) -> str:
+    import hashlib
+    return hashlib.sha256((ROOT / "paper_1909_12533_gb300" / "csrc" / name).read_bytes()).hexdigest()[:16]
+
 
 def measured_peaks() -> dict:
     p = ROOT / "MEASURED_PEAKS.json"
@@ -311,12 +322,18 @@ def main(argv=None) -> int:
     else:
         pk = peaks["bf16_tflops_sustained"]
         hw_ach = hw / (sq_ms / 1e3) / 1e12 if sq_ms > 0 else 0.0
+        traffic = None
+        ref = SQUARE_TC_TRAFFIC.get((args.workload, args.slices))
+        if ref and _source_hash("square_tc.cu") == ref[0]:
+            traffic = ref[1]
         roof = {"bound": "tensor", "achieved": achieved, "peak": pk, "unit": "TFLOP/s", "frac": achieved / pk,
-                "traffic": None, "kernel": "k_square_tc<%d>" % args.slices,
+                "traffic": traffic, "kernel": "k_square_tc<%d>" % args.slices,
                 "hw_achieved": hw_ach, "hw_frac": hw_ach / pk,
                 "note": "achieved/frac count algorithmic flops (2*32^3 per tile triplet); hw_* count the "
-                        "FP16 MMAs issued (%d slice pairs per triplet plus 128x128 super-tile padding)"
-                        % (args.slices * (args.slices + 1) // 2),
+                        "FP16 MMAs issued (slice pairs s + t <= %d, pairs that multiply an all-zero panel "
+                        "slice skipped, 128x128 super-tile padding included); traffic = DRAM bytes per launch "
+                        "from ncu, null when the kernel source differs from the captured one"
+                        % (args.slices - 1),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; FP16 = BF16 rate)"}
     line = {
         "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
