@@ -299,7 +299,7 @@ struct sp2_ctx {
   Buf p_e2, p_trS, p_trX, p_n2, p_kt, keep, scanbuf, scantmp, twork, rowlo, rowhi;
   Buf dsc, dcnt, d2;
   OpBufs opx, opy;   // tensor-core operands (the adjoint uses both)
-  Buf sflag, spos, slist, errflag, scount, tcscratch;
+  Buf sflag, spos, slist, errflag, scount, tcscratch, redwork;
   // adjoint
   std::vector<Rec> recs;
   std::vector<Buf> seg;
@@ -325,7 +325,7 @@ struct sp2_ctx {
                   &fp_col, &fp_ref, &counts, &p_e2, &p_trS, &p_trX, &p_n2, &p_kt, &keep, &scanbuf, &scantmp,
                   &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &opx.sbits,
                   &opx.cnt, &opx.spos, &opx.index, &opx.head, &opx.data, &opy.sbits, &opy.cnt, &opy.spos,
-                  &opy.index, &opy.head, &opy.data, &sflag, &spos, &slist, &errflag, &scount, &tcscratch, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
+                  &opy.index, &opy.head, &opy.data, &sflag, &spos, &slist, &errflag, &scount, &tcscratch, &redwork, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
                   &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax};
     for (Buf* b : all) bufs.push_back(b);
   }
@@ -907,7 +907,8 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
         c->ck(cudaEventRecord(c->evs1, c->st), "event");
       }
       c->ensure(c->dsc, sizeof(StepScalars));
-      c->ck(launch_reduce_step(sa.part, nout, c->dsc.as<StepScalars>(), c->st), "reduce");
+      c->ensure(c->redwork, reduce_work_bytes());
+      c->ck(launch_reduce_step(sa.part, nout, c->dsc.as<StepScalars>(), c->redwork.p, c->st), "reduce");
       // X~_i = trunc(X_i, tau_i) before the stop test on e_{i-1} is known (X_i's tiles
       // live in pool[nxt] at slot = output index); X~_{i-1} keeps its own index set
       const bool more = i <= sch.n_max;

@@ -92,7 +92,8 @@ struct SquareArgs {
   Partials part;
 };
 cudaError_t launch_square_f64(const SquareArgs& a, cudaStream_t st);
-cudaError_t launch_reduce_step(const Partials& p, int64_t ntiles, StepScalars* out, cudaStream_t st);
+size_t reduce_work_bytes();
+cudaError_t launch_reduce_step(const Partials& p, int64_t ntiles, StepScalars* out, void* work, cudaStream_t st);
 
 // trunc.cu: choose the tiles to drop (Frobenius / Frob-Inf readings)
 struct TruncWork;

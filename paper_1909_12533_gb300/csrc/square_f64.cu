@@ -166,22 +166,24 @@ __global__ void __launch_bounds__(256) k_square_f64(SqDev a) {
   if (threadIdx.x == 0) a.part.ktiles[t] = nk;
 }
 
-// Fixed-order reduction: thread k sums entries k, k+1024, ... in order, then a
-// fixed tree; the result does not depend on scheduling.
-__global__ void k_reduce_step(Partials p, int64_t nt, StepScalars* out) {
-  __shared__ double s0[1024], s1[1024], s2[1024];
-  __shared__ long long s3[1024];
-  double a = 0.0, b = 0.0, c = 0.0;
-  long long k = 0;
-  for (int64_t i = threadIdx.x; i < nt; i += 1024) {
-    a += p.e2[i];
-    b += p.trS[i];
-    c += p.trX[i];
-    k += p.ktiles[i];
-  }
+// Fixed-order two-level reduction of the per-tile partials.  Block g sums the
+// contiguous range [g c, (g+1) c), c = ceil(nt / RED_BLOCKS): thread k takes
+// entries k, k + 256, ... of the range in order, then a fixed tree; one block
+// then sums the RED_BLOCKS results with the same tree.  The result depends on
+// nt only, not on scheduling.
+constexpr int RED_BLOCKS = 256;
+
+struct RedPart {
+  double e2, trS, trX;
+  long long k;
+};
+
+__device__ void block_tree(double a, double b, double c, long long k, RedPart* out) {
+  __shared__ double s0[256], s1[256], s2[256];
+  __shared__ long long s3[256];
   s0[threadIdx.x] = a; s1[threadIdx.x] = b; s2[threadIdx.x] = c; s3[threadIdx.x] = k;
   __syncthreads();
-  for (int h = 512; h > 0; h >>= 1) {
+  for (int h = 128; h > 0; h >>= 1) {
     if ((int)threadIdx.x < h) {
       s0[threadIdx.x] += s0[threadIdx.x + h];
       s1[threadIdx.x] += s1[threadIdx.x + h];
@@ -190,11 +192,33 @@ __global__ void k_reduce_step(Partials p, int64_t nt, StepScalars* out) {
     }
     __syncthreads();
   }
+  if (threadIdx.x == 0) *out = RedPart{s0[0], s1[0], s2[0], s3[0]};
+}
+
+__global__ void __launch_bounds__(256) k_reduce_part(Partials p, int64_t nt, RedPart* part) {
+  const int64_t c = (nt + RED_BLOCKS - 1) / RED_BLOCKS;
+  const int64_t lo = (int64_t)blockIdx.x * c, hi = min(nt, lo + c);
+  double a = 0.0, b = 0.0, d = 0.0;
+  long long k = 0;
+  for (int64_t i = lo + threadIdx.x; i < hi; i += 256) {
+    a += p.e2[i];
+    b += p.trS[i];
+    d += p.trX[i];
+    k += p.ktiles[i];
+  }
+  block_tree(a, b, d, k, &part[blockIdx.x]);
+}
+
+__global__ void __launch_bounds__(256) k_reduce_step(const RedPart* __restrict__ part, StepScalars* out) {
+  const RedPart q = part[threadIdx.x];   // RED_BLOCKS == blockDim.x
+  __shared__ RedPart r;
+  block_tree(q.e2, q.trS, q.trX, q.k, &r);
+  __syncthreads();
   if (threadIdx.x == 0) {
-    out->e2 = s0[0];
-    out->trS = s1[0];
-    out->trX = s2[0];
-    out->triplets = s3[0];
+    out->e2 = r.e2;
+    out->trS = r.trS;
+    out->trX = r.trX;
+    out->triplets = r.k;
   }
 }
 
@@ -216,8 +240,13 @@ cudaError_t launch_square_f64(const SquareArgs& a, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_reduce_step(const Partials& p, int64_t ntiles, StepScalars* out, cudaStream_t st) {
-  { ++g_launches; k_reduce_step<<<1, 1024, 0, st>>>(p, ntiles, out); }
+size_t reduce_work_bytes() { return RED_BLOCKS * sizeof(RedPart); }
+
+cudaError_t launch_reduce_step(const Partials& p, int64_t ntiles, StepScalars* out, void* work, cudaStream_t st) {
+  RedPart* part = static_cast<RedPart*>(work);
+  g_launches += 2;
+  k_reduce_part<<<RED_BLOCKS, 256, 0, st>>>(p, ntiles, part);
+  k_reduce_step<<<1, RED_BLOCKS, 0, st>>>(part, out);
   return cudaGetLastError();
 }
 

@@ -216,47 +216,59 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 //   byte offset = s * 8192 + q * 2048 + g * 512 + c * 128 + r * 16 + j * 2
 // for the element in row 8g + r, column 8c + j of tile q, slice s.  The header
 // byte holds the first slice that is not all zero in any of the 4 tiles (k if
-// none) in bits 0-2 and the tiles present in bits 4-7.
+// none) in bits 0-2 and the tiles present in bits 4-7; units below that slice
+// are all zero, are never read, and are not written.
 template <int K>
 __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ index, const int32_t* __restrict__ slot,
                                                        const double* __restrict__ pool, __half* data,
                                                        uint8_t* head, int32_t* err, int lscale) {
   __shared__ __align__(16) __half sm[K * 4 * TE];
   __shared__ uint32_t wnz[8];
+  __shared__ int first_s;
   const int64_t e = blockIdx.x;
   const uint4 iw = index[e];
   const uint32_t wd[4] = {iw.x, iw.y, iw.z, iw.w};
   constexpr int FIN = 11 * K - 1;                  // finest grid 2^-FIN
+  constexpr int PER = TE / 256;                    // elements of a tile per thread
+  // all loads first (16 per thread), then the integer work
+  long long xb[4][PER];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    const bool present = wd[q] != 0xFFFFFFFFu;
+    const double* src = present ? pool + (int64_t)slot[wd[q] & ~REF_T] * TE : nullptr;
+#pragma unroll
+    for (int k = 0; k < PER; ++k) xb[q][k] = present ? __double_as_longlong(src[threadIdx.x + 256 * k]) : 0ll;
+  }
   uint32_t nz = 0;                                 // bit s: slice s has a nonzero element
   uint32_t pres = 0;
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
-    const bool present = wd[q] != 0xFFFFFFFFu;
-    pres |= (present ? 1u : 0u) << q;
+    pres |= (wd[q] != 0xFFFFFFFFu ? 1u : 0u) << q;
     const bool tr = (wd[q] & REF_T) != 0;
-    const double* src = present ? pool + (int64_t)slot[wd[q] & ~REF_T] * TE : nullptr;
-    for (int i = threadIdx.x; i < TE; i += blockDim.x) {
+#pragma unroll
+    for (int k = 0; k < PER; ++k) {
+      const int i = threadIdx.x + 256 * k;
       // stored element (i / 32, i % 32) is element (r, c) of the panel's tile
       const int r = tr ? (i & 31) : (i >> 5), c = tr ? (i >> 5) : (i & 31);
       // v = x / scale * 2^FIN rounded to the nearest integer (ties to even),
       // from the bits of x = m 2^(ex - 1075): v = m >> sh on the integer pipes
-      const long long xb = present ? __double_as_longlong(src[i]) : 0ll;
-      const int ex = (int)((xb >> 52) & 0x7FF);
+      const long long x = xb[q][k];
+      const int ex = (int)((x >> 52) & 0x7FF);
       long long v = 0;
       if (ex - lscale >= 1024) {           // |x / scale| >= 2, inf or NaN: flagged, clamped
         if (err) atomicOr(err, 4);
         v = (1ll << (FIN + 1)) - 1;
-        if (xb < 0) v = -v;
+        if (x < 0) v = -v;
       } else if (ex != 0) {
-        const unsigned long long m = ((unsigned long long)xb & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
+        const unsigned long long m = ((unsigned long long)x & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
         const int sh = 1075 + lscale - FIN - ex;   // >= 9 here
-        unsigned long long q = 0;
+        unsigned long long qv = 0;
         if (sh < 64) {
-          q = m >> sh;
+          qv = m >> sh;
           const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
-          if (rem > half || (rem == half && (q & 1ull))) ++q;
+          if (rem > half || (rem == half && (qv & 1ull))) ++qv;
         }
-        v = xb < 0 ? -(long long)q : (long long)q;
+        v = x < 0 ? -(long long)qv : (long long)qv;
       }
       int T[K];
 #pragma unroll
@@ -280,11 +292,15 @@ __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ 
   if (threadIdx.x == 0) {
     uint32_t m = 0;
     for (int w = 0; w < 8; ++w) m |= wnz[w];
-    head[e] = (uint8_t)((m ? __ffs(m) - 1 : K) | (pres << 4));
+    const int f = m ? __ffs(m) - 1 : K;
+    first_s = f;
+    head[e] = (uint8_t)(f | (pres << 4));
   }
+  __syncthreads();
+  // units below the first nonzero slice are all zero and never read: not written
   const uint4* s4 = reinterpret_cast<const uint4*>(sm);
   uint4* d4 = reinterpret_cast<uint4*>(data + e * (int64_t)(K * 4 * TE));
-  for (int i = threadIdx.x; i < K * 4 * TE / 8; i += blockDim.x) d4[i] = s4[i];
+  for (int i = first_s * (4 * TE / 8) + threadIdx.x; i < K * 4 * TE / 8; i += blockDim.x) d4[i] = s4[i];
 }
 
 // super-row bitmap: OR of the 4 tile rows
