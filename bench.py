@@ -295,19 +295,37 @@ def main(argv=None) -> int:
 
     e2e = None
     if not args.no_e2e:
+        # through the public API from pinned host memory: every step uploads F, runs, and
+        # copies D back into pinned host buffers (buffers filled / allocated before timing)
+        class HostF:
+            n = Fh.n
+            brow = torch.from_numpy(Fh.brow).pin_memory()
+            bcol = torch.from_numpy(Fh.bcol).pin_memory()
+            val = torch.from_numpy(Fh.val).pin_memory()
+        cap = int(st_main["nnzb_final"] * 1.25) + 1024
+        Dh = (torch.empty(cap, dtype=torch.int32).pin_memory(), torch.empty(cap, dtype=torch.int32).pin_memory(),
+              torch.empty((cap, 32, 32), dtype=torch.float64).pin_memory())
+
+        def e2e_step():
+            ctx = sp2.SP2(HostF, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"],
+                          precision=args.precision, slices=args.slices)
+            st = ctx.run()
+            out = ctx.D_host(Dh)
+            ctx.close()
+            return st, out
+
+        e2e_step()
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        ctx = sp2.SP2(Fh, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision=args.precision,
-                      slices=args.slices)
-        st = ctx.run()
-        brow, bcol, val = ctx.D_host()
-        ctx.close()
+        runs = [e2e_step() for _ in range(args.steps)]
         torch.cuda.synchronize()
-        dt = time.perf_counter() - t0
+        dt = (time.perf_counter() - t0) / args.steps
+        st, (brow, bcol, val) = runs[-1]
         h2d = Fh.val.nbytes + Fh.brow.nbytes + Fh.bcol.nbytes
-        d2h = val.nbytes + brow.nbytes + bcol.nbytes
-        e2e = {"value": st["alg_flops"] / dt / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": int(h2d),
-               "d2h_bytes_per_step": int(d2h), "seconds": dt}
+        d2h = val.numel() * 8 + brow.numel() * 4 + bcol.numel() * 4
+        e2e = {"value": sum(r[0]["alg_flops"] for r in runs) / args.steps / dt / 1e12, "unit": "TFLOP/s",
+               "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "seconds_per_step": dt,
+               "host_buffers": "pinned"}
 
     if rank != 0:
         return 0

@@ -224,9 +224,9 @@ void sp2_destroy(sp2_ctx* ctx);
 const char* sp2_strerror(int code);
 
 /* Not in the paper: hand the device memory cached by the library's memory
- * pools (memory of destroyed contexts, kept for reuse) back to the driver,
- * after the work queued on every device has finished.  Contexts alive keep
- * their memory.  Errors: CUDA. */
+ * pools (memory of destroyed contexts, kept for reuse) and its cached
+ * page-locked host blocks back to the driver, after the work queued on every
+ * device has finished.  Contexts alive keep their memory.  Errors: CUDA. */
 int sp2_release_memory(void);
 
 #ifdef __cplusplus

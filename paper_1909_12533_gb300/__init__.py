@@ -202,19 +202,34 @@ def sp2_get_D(ctx) -> sp2_bsr:
     return v
 
 
-def sp2_copy_D(ctx):
-    """Host copy of D: (brow, bcol, val) numpy arrays."""
+def sp2_copy_D(ctx, out=None):
+    """Host copy of D: (brow, bcol, val).  Without ``out``, new numpy arrays;
+    with ``out`` = (brow, bcol, val) host buffers (numpy arrays or CPU torch
+    tensors, e.g. pinned, with room for at least nnzb tiles) the tiles are copied
+    into them and views of length nnzb are returned."""
     n = c_int64()
     rc = load().sp2_copy_D(ctx, None, None, None, 0, 0, byref(n))
     if rc not in (SP2_OK, -10):
         raise SP2Error(rc, "sp2_copy_D")
-    brow = np.empty(n.value, np.int32)
-    bcol = np.empty(n.value, np.int32)
-    val = np.empty((n.value, TILE, TILE), np.float64)
-    rc = load().sp2_copy_D(ctx, brow.ctypes.data, bcol.ctypes.data, val.ctypes.data, n.value, 0, byref(n))
+    if out is None:
+        brow = np.empty(n.value, np.int32)
+        bcol = np.empty(n.value, np.int32)
+        val = np.empty((n.value, TILE, TILE), np.float64)
+    else:
+        brow, bcol, val = out
+        if brow.shape[0] < n.value or bcol.shape[0] < n.value or val.shape[0] < n.value:
+            raise ValueError("output buffers hold fewer tiles than D")
+        for x, kind in ((brow, "int32"), (bcol, "int32"), (val, "float64")):
+            if str(x.dtype).split(".")[-1] != kind or not (x.flags["C_CONTIGUOUS"] if isinstance(x, np.ndarray)
+                                                          else x.is_contiguous()):
+                raise ValueError("output buffers must be contiguous int32, int32, float64")
+    ptrs = [_ptr(x) for x in (brow, bcol, val)]
+    if any(d for _, d in ptrs):
+        raise ValueError("sp2_copy_D writes host buffers")
+    rc = load().sp2_copy_D(ctx, ptrs[0][0], ptrs[1][0], ptrs[2][0], n.value, 0, byref(n))
     if rc != SP2_OK:
         raise SP2Error(rc, "sp2_copy_D")
-    return brow, bcol, val
+    return brow[: n.value], bcol[: n.value], val[: n.value]
 
 
 def sp2_backward(ctx, W) -> sp2_bsr:
@@ -333,8 +348,8 @@ class SP2:
         self.stats = stats_dict(st)
         return self.stats
 
-    def D_host(self):
-        return sp2_copy_D(self.ctx)
+    def D_host(self, out=None):
+        return sp2_copy_D(self.ctx, out)
 
     def D_device(self):
         return device_view_to_torch(sp2_get_D(self.ctx))

@@ -222,6 +222,40 @@ cudaMemPool_t device_pool() {
   return g_pool[dev];
 }
 
+// Page-locked host scratch of a context (step scalars, counts): blocks of the
+// process are kept on a free list, so creating a context costs no page-locked
+// allocation after the first.
+struct HostBlock {
+  StepScalars sc;
+  int32_t cnt[4];
+  double d2[2];
+};
+std::mutex g_host_mu;
+std::vector<HostBlock*> g_host_free;
+
+HostBlock* take_host_block() {
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    if (!g_host_free.empty()) {
+      HostBlock* b = g_host_free.back();
+      g_host_free.pop_back();
+      return b;
+    }
+  }
+  void* p = nullptr;
+  if (cudaMallocHost(&p, sizeof(HostBlock)) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return static_cast<HostBlock*>(p);
+}
+
+void give_host_block(HostBlock* b) {
+  if (!b) return;
+  std::lock_guard<std::mutex> lk(g_host_mu);
+  g_host_free.push_back(b);
+}
+
 struct Alloc {
   sp2_allocator a{};
   bool custom = false;
@@ -307,6 +341,7 @@ struct sp2_ctx {
   Buf amax;
   FullPattern fpB;
   double backward_ms = 0.0;
+  HostBlock* hb = nullptr;
   StepScalars* h_sc = nullptr;
   int32_t* h_cnt = nullptr;
   double* h_d2 = nullptr;
@@ -672,6 +707,11 @@ int sp2_default_params(sp2_params* p) {
 }
 
 int sp2_release_memory(void) {
+  {
+    std::lock_guard<std::mutex> lk(g_host_mu);
+    for (HostBlock* b : g_host_free) cudaFreeHost(b);
+    g_host_free.clear();
+  }
   std::lock_guard<std::mutex> lk(g_pool_mu);
   int prev = 0;
   if (cudaGetDevice(&prev) != cudaSuccess) {
@@ -759,9 +799,11 @@ int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, d
     c->ck(cudaEventCreate(&c->ev1), "event");
     c->ck(cudaEventCreate(&c->evs0), "event");
     c->ck(cudaEventCreate(&c->evs1), "event");
-    c->ck(cudaMallocHost(&c->h_sc, sizeof(StepScalars)), "host alloc");
-    c->ck(cudaMallocHost(&c->h_cnt, 16), "host alloc");
-    c->ck(cudaMallocHost(&c->h_d2, 16), "host alloc");
+    c->hb = take_host_block();
+    if (!c->hb) throw Fail{SP2_ERR_OOM};
+    c->h_sc = &c->hb->sc;
+    c->h_cnt = c->hb->cnt;
+    c->h_d2 = c->hb->d2;
     const int64_t nnzb = F->nnzb;
     const cudaMemcpyKind kind = F->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     c->ensure(c->f_brow, nnzb * 4);
@@ -783,12 +825,7 @@ int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, d
     if (c->h_cnt[1] != c->nb) throw Fail{SP2_ERR_PATTERN};
     if (c->h_cnt[0] & 2) throw Fail{SP2_ERR_NONFINITE};
     // slots of F are the identity
-    {
-      std::vector<int32_t> id(nnzb);
-      for (int64_t i = 0; i < nnzb; ++i) id[i] = (int32_t)i;
-      c->ck(cudaMemcpyAsync(c->f_slot.p, id.data(), nnzb * 4, cudaMemcpyHostToDevice, c->st), "slots");
-      c->sync();
-    }
+    c->ck(launch_iota(c->f_slot.as<int32_t>(), nnzb, c->st), "slots");
     set_tiles(c->F, c->f_brow, c->f_bcol, c->f_slot, c->f_rowptr, nnzb);
     c->ck(launch_rowptr_from_brow(c->F.brow, nnzb, c->nb, c->F.rowptr, c->st), "rowptr");
     // Gershgorin (Section 4, Step 1)
@@ -1278,9 +1315,7 @@ void sp2_destroy(sp2_ctx* c) {
     b->p = nullptr;
   }
   cudaStreamSynchronize(c->st);
-  if (c->h_sc) cudaFreeHost(c->h_sc);
-  if (c->h_cnt) cudaFreeHost(c->h_cnt);
-  if (c->h_d2) cudaFreeHost(c->h_d2);
+  give_host_block(c->hb);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->evs0) cudaEventDestroy(c->evs0);

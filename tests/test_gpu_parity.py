@@ -160,3 +160,22 @@ def test_run_twice_is_deterministic():
     ctx.close()
     assert s1["e"] == s2["e"] and s1["t"] == s2["t"]
     assert all(np.array_equal(a, b) for a, b in zip(d1, d2))
+
+
+def test_contexts_reuse_pooled_memory_and_release():
+    # contexts created one after another reuse the library's memory pool; the
+    # results do not depend on what the pool held before; release returns it
+    import paper_1909_12533_gb300 as sp2
+    c = make_config("2s")
+    runs = [run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"]) for _ in range(2)]
+    assert np.array_equal(runs[0]["val"], runs[1]["val"])
+    sp2.sp2_release_memory()
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], precision="split16")
+    assert g["code"] == 0
+    buf = (np.empty(g["brow"].shape[0] + 5, np.int32), np.empty(g["brow"].shape[0] + 5, np.int32),
+           np.empty((g["brow"].shape[0] + 5, 32, 32)))
+    ctx = sp2.SP2(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], precision="split16")
+    ctx.run()
+    brow, bcol, val = ctx.D_host(buf)
+    ctx.close()
+    assert np.array_equal(brow, g["brow"]) and np.array_equal(val, g["val"])
