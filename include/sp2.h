@@ -113,6 +113,10 @@ typedef struct {
                               for the last four squares up to n_max + 1, the squares run in
                               FP64, so the final idempotency steps reach FP64 accuracy;
                               0 = never; default 1e-4                                   */
+  int32_t acc_flush_min;   /* SPLIT16: a 128 x 128 output block whose product has at least this many
+                              K tiles adds its FP32 tensor-memory sums into the exact fixed-point
+                              total every 16 K tiles (keeps the sums exact for dense operands);
+                              0 = never; default 512                                    */
 } sp2_params;
 
 typedef struct {

@@ -46,7 +46,8 @@ class sp2_params(ctypes.Structure):
     _fields_ = [("mode", c_int32), ("stop", c_int32), ("idem_tol", c_double), ("trunc", c_int32),
                 ("frobinf_part", c_int64), ("gamma", c_double), ("delta_acc", c_double), ("n_max_cap", c_int32),
                 ("precision", c_int32), ("slices", c_int32), ("mixed_from", c_int32), ("mixed_until", c_int32),
-                ("ckpt_every", c_int32), ("record_masks", c_int32), ("fp64_tail", c_double)]
+                ("ckpt_every", c_int32), ("record_masks", c_int32), ("fp64_tail", c_double),
+                ("acc_flush_min", c_int32)]
 
 
 class sp2_stats(ctypes.Structure):

@@ -639,6 +639,7 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   L.words = c->words;
   c->ensure(c->tcscratch, (size_t)nsuper * 2 * 128 * 128 * 8);
   L.scratch = c->tcscratch.p;
+  L.seg_min = c->prm.acc_flush_min;
   L.err = c->errflag.as<int32_t>();
   c->ck(cudaEventRecord(c->evs0, c->st), "event");
   c->ck(launch_square_tc(L, c->st), "square tc");
@@ -703,6 +704,7 @@ int sp2_default_params(sp2_params* p) {
   p->ckpt_every = 8;
   p->record_masks = 0;
   p->fp64_tail = 1e-4;
+  p->acc_flush_min = 512;
   return SP2_OK;
 }
 
@@ -767,6 +769,7 @@ int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, d
   if (prm.mode != SP2_MODE_SP2 && prm.mode != SP2_MODE_SP2ACC) return SP2_ERR_INVALID_ARG;
   if (prm.stop != SP2_STOP_PARAMETERLESS && prm.stop != SP2_STOP_IDEMPOTENCY) return SP2_ERR_INVALID_ARG;
   if (!(prm.fp64_tail >= 0.0) || !std::isfinite(prm.fp64_tail)) return SP2_ERR_INVALID_ARG;
+  if (prm.acc_flush_min < 0) return SP2_ERR_INVALID_ARG;
   if (prm.trunc != SP2_TRUNC_FROBENIUS && prm.trunc != SP2_TRUNC_FROBINF) return SP2_ERR_INVALID_ARG;
   if (prm.trunc == SP2_TRUNC_FROBINF && (prm.frobinf_part < TB || prm.frobinf_part % TB)) return SP2_ERR_INVALID_ARG;
   if (prm.n_max_cap < 1 || prm.n_max_cap > SP2_MAX_ITER - 2) return SP2_ERR_INVALID_ARG;
@@ -953,12 +956,15 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       if (more) next = truncate_launch(c, c->out, c->p_n2.as<double>(), sch.tau[i], 1 - c->xset);
       // one host round trip per step: scalars, error flags, kept-tile count
       c->ck(cudaMemcpyAsync(c->h_sc, c->dsc.p, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->st), "d2h");
-      c->ck(cudaMemcpyAsync(c->h_cnt + 2, c->errflag.p, 4, cudaMemcpyDeviceToHost, c->st), "d2h");
+      c->ck(cudaMemcpyAsync(c->h_cnt + 2, c->errflag.p, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
       c->ck(cudaMemcpyAsync(c->h_d2, c->errflag.as<char>() + 8, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
       if (more) c->ck(cudaMemcpyAsync(c->h_cnt, c->dcnt.p, 4, cudaMemcpyDeviceToHost, c->st), "d2h");
       c->sync();
       if (c->h_cnt[2] & 1) {
-        c->last_error = "tensor-core square: a bounded wait timed out";
+        char sites[16];
+        snprintf(sites, sizeof sites, "0x%x", (unsigned)c->h_cnt[3]);
+        c->last_error = std::string("tensor-core square: a bounded wait timed out (sites ") + sites + ")";
+        fprintf(stderr, "sp2_run: %s\n", c->last_error.c_str());
         throw Fail{SP2_ERR_TIMEOUT};
       }
       if (tc) {

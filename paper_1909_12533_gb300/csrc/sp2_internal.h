@@ -145,6 +145,7 @@ struct TcLaunch {
   int nb, nsr, k, words;
   int32_t* err;
   void* scratch;             // nsuper * 2 * 128 * 128 int64 (epilogue staging, two tiles per CTA)
+  int seg_min;               // K loops of at least this many steps are accumulated in 16-step segments (0: never)
 };
 size_t panel_record_bytes(int k);
 cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32_t* slot, const double* pool,

@@ -105,6 +105,13 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
   return ok != 0;
 }
 
+// Timeout sites of a launch, for the error message (err[1], bit 1 producer
+// stage, 2 producer tile slot, 3 MMA data, 4 MMA TMEM or segment slot, 5 MMA
+// drain, 6 epilogue tile, 7 epilogue segment).
+__device__ __forceinline__ void note_timeout(int32_t* err, int where) {
+  if (err) atomicOr(err + 1, 1 << where);
+}
+
 // Bounded wait with suspension between polls: false on timeout.
 __device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
@@ -396,6 +403,7 @@ struct TcArgs {
   int nb, words, nsr;
   int32_t* err;
   long long* scratch;       // per CTA, 2 slots: 128 x 128 fixed-point sums of a tile in its epilogue
+  int seg_min;              // K loops of at least this many steps are cut into 16-step segments (0: never)
 };
 
 // A pipeline stage holds one sub-step: two A units and two B units, a unit
@@ -403,7 +411,12 @@ struct TcArgs {
 // apart).  A sub-step record (32 bits) tells the MMA issuer what it holds:
 //   bits 0-1 / 2-3: slices of A units 0 / 1, bits 4-5 / 6-7: of B units 0 / 1,
 //   bits 8-11: product mask, bit (2 i + j) for A unit i x B unit j,
-//   bit 12: end of the super-tile, bit 13: no more super-tiles (no data).
+//   bit 12: end of the super-tile, bit 13: no more super-tiles, bit 14: end of an
+//   accumulation segment (no data).  A super-tile whose K loop has at least
+//   seg_min K steps closes a segment after every 16 K steps: the epilogue adds
+//   the segment's exact fixed-point sums into the scratch and frees the TMEM,
+//   so no FP32 accumulator sums more than 16 K steps (512 products per
+//   element) and the groups stay exact for dense operands.
 constexpr int UNIT_BYTES = 4 * SLICE_BYTES;
 constexpr int STAGE_BYTES = 4 * UNIT_BYTES;
 constexpr int STAGES = 6;
@@ -411,13 +424,17 @@ constexpr uint32_t REC_END = 1u << 12;
 constexpr int EPI_WARPS = 8;                       // epilogue warps 2..9
 constexpr int TC_THREADS = 32 * (2 + EPI_WARPS);   // + producer warp 0, MMA warp 1
 constexpr uint32_t REC_LAST = 1u << 13;   // no more super-tiles (no data)
+constexpr uint32_t REC_SEG = 1u << 14;    // end of an accumulation segment of the super-tile (no data)
+constexpr uint32_t SEG_LAST = 1u << 31;   // segment record flag: last segment of its super-tile
+constexpr int SEG_RING = 4;               // accumulation segments in flight between MMA and epilogue
+constexpr int SEG_KSTEPS = 16;            // K steps per accumulation segment of a segmented tile
 
 // record header byte: first nonzero slice (bits 0-2), tiles present (bits 4-7)
 constexpr uint32_t HEAD_NONE = 0x07u;   // header of a K index outside the step list
 
 template <int K>
 struct TcCfg {
-  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 96 * 16;
+  static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 128 * 16;
   // unit of the finest group, 2^-(11 (k + 1) - 2)
   static constexpr double UNIT = 1.0 / (double)(1ull << (11 * (K + 1) - 2));
 };
@@ -430,18 +447,18 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   unsigned char* stage_base = smem_raw;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;     // [2] MMAs of the tile done (commit) + group map written
-  uint64_t* tile_full = acc_full + 2;      // [2] tile slot written by the producer
+  uint64_t* acc_full = empty + STAGES;     // [SEG_RING] MMAs of a segment done (commit) + its record written
+  uint64_t* tile_full = acc_full + SEG_RING;   // [2] tile slot written by the producer
   uint64_t* tile_empty = tile_full + 2;    // [2] epilogue done with the tile slot (one arrive per warp)
   uint64_t* drain = tile_empty + 2;        // MMAs issued before the exit are complete
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(drain + 1);
+  uint64_t* tmem_empty = drain + 1;        // [SEG_RING] every epilogue warp has read the segment's TMEM
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + SEG_RING);
   int32_t* tslot = reinterpret_cast<int32_t*>(tmem_slot + 2);      // [2] super-tile list index, -1: none
   int32_t* kcount = tslot + 2;                                      // [2][16] triplets per output tile
-  uint32_t* gmap = reinterpret_cast<uint32_t*>(kcount + 32);       // [2] groups written, block of each
-  uint32_t* rec = gmap + 2;                                         // [STAGES] sub-step records
+  uint32_t* gmap = reinterpret_cast<uint32_t*>(kcount + 32);       // [SEG_RING] groups written, block of each, last flag
+  uint32_t* rec = gmap + SEG_RING;                                  // [STAGES] sub-step records
   int32_t* status = reinterpret_cast<int32_t*>(rec + STAGES);      // [0] a wait timed out
-  uint4* ulist = reinterpret_cast<uint4*>(smem_raw + STAGES * STAGE_BYTES + 1024);   // [96] sub-steps of a batch
-  uint32_t* tfree = reinterpret_cast<uint32_t*>(status + 1);       // TMEM blocks released (warps x tiles)
+  uint4* ulist = reinterpret_cast<uint4*>(smem_raw + STAGES * STAGE_BYTES + 1024);   // [128] sub-steps of a batch
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -449,15 +466,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       mbar_init(&full[s], 1);
       mbar_init(&empty[s], 1);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < SEG_RING; ++b) {
       mbar_init(&acc_full[b], 2);
+      mbar_init(&tmem_empty[b], EPI_WARPS);
+    }
+    for (int b = 0; b < 2; ++b) {
       mbar_init(&tile_full[b], 1);
       mbar_init(&tile_empty[b], EPI_WARPS);
     }
     mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     status[0] = 0;
-    *tfree = 0u;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
@@ -484,16 +503,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
     // its own copy of the stage counter; no warp votes per sub-step.
     int step = 0;
     bool ok = true;
-    // lanes 0-3: one sub-step (srcA / srcB: the K step's A and B panel records)
+    // lanes 0-3: one sub-step (srcA / srcB: the K step's A and B panel records).
+    // Lane 0 waits for the stage and the others take its result, so the four
+    // lanes stay on the same stage phase.
     auto emit = [&](uint32_t rv, const __half* srcA, const __half* srcB) -> bool {
       const int s = step % STAGES;
       const uint32_t par = ((step / STAGES) & 1) ^ 1;
       ++step;
-      if (!mbar_wait(&empty[s], par)) {
-        status[0] = 1;
+      int good = 1;
+      if (lane == 0) good = mbar_wait(&empty[s], par) ? 1 : 0;
+      good = __shfl_sync(0xFu, good, 0);
+      if (!good) {
+        if (lane == 0) {
+          status[0] = 1;
+          note_timeout(a.err, 1);
+        }
         return false;
       }
-      const uint32_t mask = (rv & (REC_END | REC_LAST)) ? 0u : (rv >> 8) & 0xFu;
+      const uint32_t mask = (rv & (REC_END | REC_LAST | REC_SEG)) ? 0u : (rv >> 8) & 0xFu;
       // units A0, A1, B0, B1 read by a product of the mask
       const uint32_t use = ((mask & 0x3u) ? 1u : 0u) | ((mask & 0xCu) ? 2u : 0u) | ((mask & 0x5u) ? 4u : 0u) |
                            ((mask & 0xAu) ? 8u : 0u);
@@ -507,10 +534,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
                  &full[s]);
       return true;
     };
-    // all lanes: a control sub-step (no data), issued by lane 0
+    // all lanes: a control sub-step (no data) through lanes 0-3
     auto emit_ctl = [&](uint32_t rv) -> bool {
       bool r = true;
-      if (lane == 0) r = emit(rv, nullptr, nullptr);
+      if (lane < 4) r = emit(rv, nullptr, nullptr);
       else ++step;
       return __shfl_sync(FULLW, r ? 1 : 0, 0) != 0;
     };
@@ -521,7 +548,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       if (lane == 0) good = mbar_wait_sleep(&tile_empty[b], (((uint32_t)it >> 1) & 1u) ^ 1u) ? 1 : 0;
       good = __shfl_sync(FULLW, good, 0);
       if (!good) {
-        if (lane == 0) status[0] = 1;
+        if (lane == 0) { status[0] = 1; note_timeout(a.err, 2); }
         break;
       }
       int idx = 0;
@@ -538,6 +565,24 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       }
       const int stile = a.list[idx];
       const int R = stile / a.nsr, C = stile % a.nsr;
+      // the epilogue learns the tile now (it drains segments while the tile is produced)
+      if (lane == 0) {
+        tslot[b] = idx;
+        mbar_arrive(&tile_full[b]);
+      }
+      // K steps of the tile (both passes): long K loops are cut into segments
+      int ktot = 0;
+      if (a.seg_min > 0) {
+        for (int pass = 0; pass < 1 + a.two_pass; ++pass) {
+          const TcOperand& oa = pass == 0 ? a.P : a.Q;
+          const TcOperand& ob = pass == 0 ? a.Q : a.P;
+          for (int w = lane; w < a.words; w += 32)
+            ktot += __popc(oa.sbits[(int64_t)R * a.words + w] & ob.sbits[(int64_t)C * a.words + w]);
+        }
+        ktot = __reduce_add_sync(FULLW, ktot);
+      }
+      const bool segmented = a.seg_min > 0 && ktot >= a.seg_min;
+      int kdone = 0;
       int kc = 0;   // lane t < 16: K steps with A tile t / 4 and B tile t % 4 both present
       for (int pass = 0; pass < 1 + a.two_pass && ok; ++pass) {
         // pass 0: A = P (rows I), B = Q (rows J); pass 1: A = Q, B = P
@@ -624,7 +669,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
                 ++ns;
               }
             }
-            int soff = ns;
+            // a segmented tile also closes a segment before K steps 16 of the batch
+            const int lead = (segmented && lane == SEG_KSTEPS && jb + lane < total) ? 1 : 0;
+            int soff = ns + lead;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
               const int v = __shfl_up_sync(FULLW, soff, o);
@@ -632,6 +679,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             }
             const int nsub = __shfl_sync(FULLW, soff, 31);
             soff -= ns;
+            if (lead) ulist[soff - 1] = make_uint4(REC_SEG, 0u, 0u, 0u);
             if (ns > 0) ulist[soff] = make_uint4(rv0, (uint32_t)ea, (uint32_t)eb, 0u);
             if (ns > 1) ulist[soff + 1] = make_uint4(rv1, (uint32_t)ea, (uint32_t)eb, 0u);
             if (ns > 2) ulist[soff + 2] = make_uint4(rv2, (uint32_t)ea, (uint32_t)eb, 0u);
@@ -651,6 +699,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             }
             ok = __all_sync(FULLW, lok);
             __syncwarp();   // the list is rebuilt for the next batch
+            kdone += min(32, total - jb);
+            if (segmented && ok && kdone < ktot) ok = emit_ctl(REC_SEG);
             ea = ea_n;
             eb = eb_n;
             ha = ha_n;
@@ -658,50 +708,55 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           }
         }
       }
-      if (ok) ok = emit_ctl(REC_END);
+      // counts before the end record: the record's barrier, then the segment's,
+      // order them before the epilogue's reads
       if (lane < 16) kcount[b * 16 + lane] = kc;
-      if (lane == 0) tslot[b] = idx;
       __syncwarp();
-      if (lane == 0) mbar_arrive(&tile_full[b]);   // release: slot and counts visible to the epilogue
+      if (ok) ok = emit_ctl(REC_END);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer.  TMEM is four blocks of 128 columns; a group
-    // accumulator of a tile takes a free block on its first product, and the
-    // blocks of a tile return to the pool once all epilogue warps have read
-    // them (tfree counts warp releases, EPI_WARPS per tile, in tile order).
+    // accumulator of a segment (a whole super-tile, or 32 of its K steps) takes
+    // a free block on its first product, and the blocks of a segment return to
+    // the pool once every epilogue warp has read them (one arrival per warp on
+    // the segment slot's tmem_empty barrier; segments are reclaimed in order).
     int step = 0;
     uint32_t free_mask = 0xFu;
-    uint32_t pend0 = 0u, pend1 = 0u;   // blocks held by the tile in slot 0 / 1 until released
-    int released = 0;              // tiles whose blocks are back in free_mask
+    // blocks held by the segment in each ring slot (4 slots)
+    uint32_t pend0 = 0u, pend1 = 0u, pend2 = 0u, pend3 = 0u;
+    int released = 0;              // segments whose blocks are back in free_mask
+    int seg = 0;                   // segments published
     unsigned long long nprod = 0;
     bool ok = true, done = false;
-    // take back the blocks of the oldest tile that still holds some; false on timeout
+    // take back the blocks of the oldest segment that still holds some; false on timeout
     auto reclaim = [&]() -> bool {
-      const unsigned long long t0 = now_ns();
-      while (*(volatile uint32_t*)tfree < (uint32_t)EPI_WARPS * (uint32_t)(released + 1)) {
-        if (now_ns() - t0 > WAIT_NS) return false;
-        __nanosleep(100);
+      if (!mbar_wait(&tmem_empty[released & (SEG_RING - 1)], ((uint32_t)released >> 2) & 1u)) {
+        note_timeout(a.err, 4);
+        return false;
       }
-      __threadfence_block();
       tc_fence_after();
-      if (released & 1) { free_mask |= pend1; pend1 = 0u; }
-      else { free_mask |= pend0; pend0 = 0u; }
+      switch (released & (SEG_RING - 1)) {
+        case 0: free_mask |= pend0; pend0 = 0u; break;
+        case 1: free_mask |= pend1; pend1 = 0u; break;
+        case 2: free_mask |= pend2; pend2 = 0u; break;
+        default: free_mask |= pend3; pend3 = 0u; break;
+      }
       ++released;
       return true;
     };
-    for (int it = 0; ok && !done; ++it) {
-      const int b = it & 1;
+    while (ok && !done) {
       uint32_t written = 0, gblk = 0, used = 0;
+      uint32_t kind = 0;
       for (;;) {
         const int s = step % STAGES;
         const uint32_t par = (step / STAGES) & 1;
         ++step;
-        if (!mbar_wait(&full[s], par)) { ok = false; break; }
+        if (!mbar_wait(&full[s], par)) { ok = false; note_timeout(a.err, 3); break; }
         tc_fence_after();
         const uint32_t rv = rec[s];
-        if (rv & (REC_END | REC_LAST)) {
+        if (rv & (REC_END | REC_LAST | REC_SEG)) {
           mma_commit(&empty[s]);
-          done = (rv & REC_LAST) != 0;
+          kind = rv & (REC_END | REC_LAST | REC_SEG);
           break;
         }
         const uint32_t sbase = smem_u32(stage_base + s * STAGE_BYTES);
@@ -725,7 +780,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             for (int kk = 0; kk < 2; ++kk) {
               const uint64_t ad = make_desc(sbase + i * UNIT_BYTES + kk * 256, 128, 512);
               const uint64_t bd = make_desc(sbase + (2 + j) * UNIT_BYTES + kk * 256, 128, 512);
-              // the first MMA into a group accumulator of a tile overwrites it
+              // the first MMA into a group accumulator of a segment overwrites it
               mma_f16(dcol, ad, bd, (kk > 0 || acc) ? 1u : 0u);
             }
             written |= 1u << g;
@@ -736,21 +791,29 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
         mma_commit(&empty[s]);
         if (!ok) break;
       }
-      if (!ok || done) break;
-      // the slot's previous tile (it - 2) has been released by now: the producer
-      // started this tile only after the epilogue finished that one
-      while (released < it - 1 && ok) ok = reclaim();
-      if (b) pend1 = used;
-      else pend0 = used;
-      gmap[b] = written | (gblk << 8);
-      mma_commit(&acc_full[b]);    // arrives once every MMA of the tile has completed
-      mbar_arrive(&acc_full[b]);   // release: group map visible to the epilogue
+      if (!ok) break;
+      if (kind & REC_LAST) { done = true; break; }
+      // publish the segment in ring slot seg % SEG_RING once the segment that used
+      // the slot before has been read and its blocks reclaimed
+      while (released < seg - (SEG_RING - 1) && ok) ok = reclaim();
+      if (!ok) break;
+      const int q = seg & (SEG_RING - 1);
+      switch (q) {
+        case 0: pend0 = used; break;
+        case 1: pend1 = used; break;
+        case 2: pend2 = used; break;
+        default: pend3 = used; break;
+      }
+      gmap[q] = written | (gblk << 8) | ((kind & REC_END) ? SEG_LAST : 0u);
+      mma_commit(&acc_full[q]);    // arrives once every MMA of the segment has completed
+      mbar_arrive(&acc_full[q]);   // release: segment record visible to the epilogue
+      ++seg;
     }
     if (!ok) status[0] = 1;
     // slice-pair products issued (each 2 MMAs of 128 x 128 x 16)
     if (a.err && nprod) atomicAdd(reinterpret_cast<unsigned long long*>(a.err + 2), nprod);
     mma_commit(drain);
-    if (!mbar_wait(drain, 0)) status[0] = 1;
+    if (!mbar_wait(drain, 0)) { status[0] = 1; note_timeout(a.err, 5); }
   } else if (warp >= 2) {
     // ---------------- epilogue (warps 2-9, two per SM sub-partition: warp w
     // reads TMEM lanes 32 (w % 4)..+31 = tile row I0 + w % 4, lane = row inside
@@ -780,68 +843,88 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       cnt = __reduce_add_sync(FULLW, cnt);
       return rowptr[row] + cnt + __popc(m & ((1u << (col & 31)) - 1u));
     };
+    int seg = 0;   // segments consumed
     for (int it = 0;; ++it) {
       const int b = it & 1;
       const uint32_t par = ((uint32_t)it >> 1) & 1u;
       bool good = true;
       if (lane == 0) good = mbar_wait_sleep(&tile_full[b], par);
       good = __shfl_sync(FULLW, good ? 1 : 0, 0) != 0;
-      if (!good) { if (lane == 0) status[0] = 1; break; }
+      if (!good) { if (lane == 0) { status[0] = 1; note_timeout(a.err, 6); } break; }
       __syncwarp();
       const int idx = tslot[b];
       if (idx < 0) break;
-      if (lane == 0) good = mbar_wait_sleep(&acc_full[b], par);
-      good = __shfl_sync(FULLW, good ? 1 : 0, 0) != 0;
-      if (!good) { if (lane == 0) status[0] = 1; break; }
-      __syncwarp();
-      tc_fence_after();
-      const uint32_t gm = gmap[b];
-      const uint32_t written = gm & 0xFu;
       const int stile = a.list[idx];
       const int R = stile / a.nsr, C = stile % a.nsr;
       const int I0 = 4 * R, J0 = 4 * C;
       const int Ia = I0 + quarter;           // tile row of this thread
       const int64_t gi = (int64_t)Ia * TB + r;
       long long* scr = a.scratch + ((int64_t)blockIdx.x * 2 + b) * (ST * ST) + (int64_t)(quarter * 32 + r) * ST;
-      // phase 1: output tile index of each column tile; TMEM -> scratch
+      // output tile index of each column tile
       int oidx[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int Jb = J0 + bt0 + h;
         oidx[h] = (Ia < a.nb && Jb < a.nb && Ia <= Jb) ? find(a.obits, a.orowptr, Ia, Jb) : -1;
       }
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int bt = bt0 + h;
-        if (oidx[h] < 0) continue;      // warp-uniform
-#pragma unroll
-        for (int ch = 0; ch < 2; ++ch) {
-          const int col0 = bt * 32 + ch * 16;
-          long long fx[16];
-#pragma unroll
-          for (int i = 0; i < 16; ++i) fx[i] = 0;
-#pragma unroll
-          for (int gg = 0; gg < K; ++gg) {
-            if ((written >> gg) & 1u) {   // warp-uniform: groups no product reached are zero
-              float g[16];
-              const uint32_t blk = (gm >> (8 + 2 * gg)) & 3u;
-              tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + blk * ST + (uint32_t)col0, g);
-#pragma unroll
-              for (int i = 0; i < 16; ++i) fx[i] += f32_int_to_ll(g[i]) * (1ll << (11 * (K - 1 - gg)));
-            }
-          }
-          longlong2* sp = reinterpret_cast<longlong2*>(scr + col0);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) sp[i] = make_longlong2(fx[2 * i], fx[2 * i + 1]);
+      // phase 1, once per accumulation segment: TMEM -> the exact fixed-point
+      // sums of this thread's row in the scratch (the first segment stores, the
+      // others add), then the segment's TMEM blocks go back to the MMA issuer
+      for (bool first = true;; first = false) {
+        const int q = seg & (SEG_RING - 1);
+        const uint32_t spar = ((uint32_t)seg >> 2) & 1u;
+        if (lane == 0) good = mbar_wait_sleep(&acc_full[q], spar);
+        good = __shfl_sync(FULLW, good ? 1 : 0, 0) != 0;
+        if (!good) {
+          if (lane == 0) note_timeout(a.err, 7);
+          break;
         }
+        __syncwarp();
+        tc_fence_after();
+        const uint32_t gm = gmap[q];
+        const uint32_t written = gm & 0xFu;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int bt = bt0 + h;
+          if (oidx[h] < 0) continue;      // warp-uniform
+#pragma unroll
+          for (int ch = 0; ch < 2; ++ch) {
+            const int col0 = bt * 32 + ch * 16;
+            long long fx[16];
+            longlong2* sp = reinterpret_cast<longlong2*>(scr + col0);
+            if (first) {
+#pragma unroll
+              for (int i = 0; i < 16; ++i) fx[i] = 0;
+            } else {
+#pragma unroll
+              for (int i = 0; i < 8; ++i) {
+                const longlong2 t2 = sp[i];
+                fx[2 * i] = t2.x;
+                fx[2 * i + 1] = t2.y;
+              }
+            }
+#pragma unroll
+            for (int gg = 0; gg < K; ++gg) {
+              if ((written >> gg) & 1u) {   // warp-uniform: groups no product reached are zero
+                float g[16];
+                const uint32_t blk = (gm >> (8 + 2 * gg)) & 3u;
+                tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + blk * ST + (uint32_t)col0, g);
+#pragma unroll
+                for (int i = 0; i < 16; ++i) fx[i] += f32_int_to_ll(g[i]) * (1ll << (11 * (K - 1 - gg)));
+              }
+            }
+#pragma unroll
+            for (int i = 0; i < 8; ++i) sp[i] = make_longlong2(fx[2 * i], fx[2 * i + 1]);
+          }
+        }
+        // this warp's TMEM reads of the segment are complete
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&tmem_empty[q]);
+        ++seg;
+        if (gm & SEG_LAST) break;
       }
-      // this warp's TMEM reads are complete: release its share of the blocks
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) {
-        __threadfence_block();
-        atomicAdd(tfree, 1u);
-      }
+      if (!good) { if (lane == 0) status[0] = 1; break; }
       // phase 2: X_new, per-tile ||X~ - S||^2, ||X_new||^2 and traces
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
@@ -1067,6 +1150,7 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   a.opool = L.opool;
   a.part = L.part; a.c0 = L.c0; a.c1 = L.c1; a.c2 = L.c2; a.scale = L.scale; a.n = L.n; a.nb = L.nb;
   a.words = L.words; a.nsr = L.nsr; a.err = L.err; a.scratch = static_cast<long long*>(L.scratch);
+  a.seg_min = L.seg_min;
   cudaError_t e = cudaSuccess;
   switch (L.k) {
     case 2:
