@@ -53,7 +53,7 @@ PEAK_FP64_TFLOPS = 1.25   # GB300 FP64 nominal (no FP64 tensor path on this chip
 # square kernel from one ncu capture of the default workload, keyed by the sha256 prefix of the
 # kernel source it was taken on; reported only while the source is unchanged
 # (profiles/k_square_tc_water24k.md has the command).
-SQUARE_TC_TRAFFIC = {("water24k", 4): ("16d97aa940846a03", 13.892e9)}
+SQUARE_TC_TRAFFIC = {("water24k", 4): ("00086e7fad37915b", 13.979e9)}
 
 
 def _source_hash(name: str) -> str:
