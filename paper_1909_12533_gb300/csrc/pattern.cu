@@ -112,6 +112,25 @@ __global__ void k_scan_apply(const int32_t* __restrict__ in, int64_t n, const in
   }
 }
 
+// n <= SCAN_CHUNK: the three passes above in one CTA.
+__global__ void k_scan_one(const int32_t* __restrict__ in, int64_t n, int32_t* out, int32_t* total_dev) {
+  int v[SCAN_PER];
+  int s = 0;
+  for (int q = 0; q < SCAN_PER; ++q) {
+    const int64_t i = (int64_t)threadIdx.x * SCAN_PER + q;
+    v[q] = (i < n) ? in[i] : 0;
+    s += v[q];
+  }
+  __shared__ int tot;
+  int ex = block_excl_scan(s, &tot);
+  for (int q = 0; q < SCAN_PER; ++q) {
+    const int64_t i = (int64_t)threadIdx.x * SCAN_PER + q;
+    if (i < n) out[i] = ex;
+    ex += v[q];
+  }
+  if (threadIdx.x == 0 && total_dev) *total_dev = tot;
+}
+
 __device__ __forceinline__ int64_t lower_bound_i32(const int32_t* a, int64_t lo, int64_t hi, int32_t key) {
   while (lo < hi) {
     int64_t mid = (lo + hi) >> 1;
@@ -235,6 +254,10 @@ cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t n, int
     return cudaSuccess;
   }
   const int64_t nch = (n + SCAN_CHUNK - 1) / SCAN_CHUNK;
+  if (nch == 1) {
+    { ++g_launches; k_scan_one<<<1, SCAN_T, 0, st>>>(in, n, out_excl, total_dev); }
+    return cudaGetLastError();
+  }
   int32_t* cs = static_cast<int32_t*>(tmp);
   { ++g_launches; k_scan_chunks<<<(unsigned)nch, SCAN_T, 0, st>>>(in, n, cs); }
   { ++g_launches; k_scan_partials<<<1, SCAN_T, 0, st>>>(cs, nch, total_dev); }

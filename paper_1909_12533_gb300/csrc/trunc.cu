@@ -18,6 +18,7 @@
 // their bit patterns -- then the 32-bit linear tile index).  Twelve passes of
 // 8 bits; each pass histograms the budget units of the remaining candidates and
 // one thread per segment walks its 256 buckets.  No sort, no host round trip.
+// A single segment of at most 2048 tiles runs the same passes in one CTA.
 #include "sp2_internal.h"
 
 namespace sp2 {
@@ -216,6 +217,120 @@ __global__ void k_mark(const int32_t* __restrict__ brow, const int32_t* __restri
   keep[t] = drop ? 0 : 1;
 }
 
+// One CTA for a single segment of at most SMALL_MAX tiles: the same twelve
+// passes as k_hist + k_select + k_mark, keys held in shared memory, so a small
+// truncation is one launch instead of about forty.  All sums are the same exact
+// integers, so the keep flags equal the multi-launch path's.
+constexpr int SMALL_MAX = 2048;
+constexpr int SMALL_THREADS = 1024;
+
+__global__ void __launch_bounds__(SMALL_THREADS)
+    k_trunc_small(const int32_t* __restrict__ brow, const int32_t* __restrict__ bcol,
+                  const int32_t* __restrict__ slot, const double* __restrict__ n2, int n, int nb, double budget,
+                  int32_t* keep) {
+  __shared__ unsigned long long s_hi[SMALL_MAX];
+  __shared__ unsigned long long s_q[SMALL_MAX];
+  __shared__ uint32_t s_lo[SMALL_MAX];
+  __shared__ unsigned long long hist[256];
+  __shared__ unsigned long long s_rem, s_ph;
+  __shared__ uint32_t s_pl;
+  __shared__ int s_state, s_depth;
+  const double sc = budget > 0.0 ? Q_SCALE / budget : 0.0;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int I = brow[t], J = bcol[t];
+    const double v = n2[slot ? slot[t] : t];
+    const double wt = (I == J) ? 1.0 : 2.0;
+    unsigned long long q;
+    if (sc == 0.0) {
+      q = (v == 0.0) ? 0ull : Q_CAP;
+    } else {
+      const double x = (wt * v) * sc;
+      q = (x >= (double)Q_CAP) ? Q_CAP : (unsigned long long)ceil(x);
+    }
+    s_hi[t] = __double_as_longlong(v);
+    s_lo[t] = (uint32_t)I * (uint32_t)nb + (uint32_t)J;
+    s_q[t] = q;
+  }
+  if (threadIdx.x == 0) {
+    s_rem = Q_BUDGET;
+    s_ph = 0ull;
+    s_pl = 0u;
+    s_state = 0;
+    s_depth = 0;
+  }
+  for (int p = 0; p < 12; ++p) {
+    for (int k = threadIdx.x; k < 256; k += blockDim.x) hist[k] = 0ull;
+    __syncthreads();
+    if (s_state != 0) break;
+    const unsigned long long ph = s_ph;
+    const uint32_t pl = s_pl;
+    for (int t = threadIdx.x; t < n; t += blockDim.x) {
+      const unsigned long long hi = s_hi[t];
+      const uint32_t lo = s_lo[t];
+      if (is_candidate(hi, lo, p, ph, pl)) atomicAdd(&hist[digit_of(hi, lo, p)], s_q[t]);
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {
+      // bucket walk of k_select: lane l owns buckets 8l..8l+7, an inclusive
+      // scan over the lanes finds the lane holding the cut
+      const int lane = threadIdx.x;
+      unsigned long long loc[8], sum = 0ull;
+#pragma unroll
+      for (int j = 0; j < 8; ++j) {
+        loc[j] = hist[lane * 8 + j];
+        sum += loc[j];
+      }
+      unsigned long long inc = sum;
+#pragma unroll
+      for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long v = __shfl_up_sync(0xffffffffu, inc, off);
+        if (lane >= off) inc += v;
+      }
+      const unsigned long long rem = s_rem;
+      const unsigned bal = __ballot_sync(0xffffffffu, inc > rem);
+      if (bal == 0u) {
+        if (lane == 0) {
+          s_state = 1;      // every candidate fits
+          s_depth = p;
+        }
+      } else if (lane == __ffs(bal) - 1) {
+        unsigned long long r = rem - (inc - sum);
+        int cut = 8 * lane + 7;
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          if (loc[j] <= r) {
+            r -= loc[j];
+          } else {
+            cut = 8 * lane + j;
+            break;
+          }
+        }
+        s_rem = r;
+        if (p < 8) s_ph = (ph << 8) | (unsigned long long)cut;
+        else s_pl = (pl << 8) | (uint32_t)cut;
+      }
+    }
+    __syncthreads();
+  }
+  __syncthreads();
+  const unsigned long long ph = s_ph;
+  const uint32_t pl = s_pl;
+  const int state = s_state, dep = s_depth;
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const unsigned long long hi = s_hi[t];
+    const uint32_t lo = s_lo[t];
+    bool drop;
+    if (state == 1) {
+      if (dep == 0) drop = true;
+      else if (dep <= 8) drop = (hi >> (64 - 8 * dep)) <= ph;
+      else drop = hi < ph || (hi == ph && (lo >> (32 - 8 * (dep - 8))) <= pl);
+    } else {
+      drop = hi < ph || (hi == ph && lo < pl);
+    }
+    keep[t] = drop ? 0 : 1;
+  }
+}
+
 // ||tile||_F^2 of contiguous tiles (fixed order: 4 strided partial sums per
 // thread, then a fixed tree), one CTA of 256 threads per tile.
 __global__ void __launch_bounds__(256) k_tile_norms(const double* __restrict__ val, double* n2) {
@@ -257,6 +372,11 @@ cudaError_t launch_truncate(const TileSet& x, const double* n2, int nb, double t
   if (nnzb == 0) return cudaSuccess;
   const int nsb = (int)((nb + part_tiles - 1) / part_tiles);
   const int64_t nseg = mode == 1 ? (int64_t)nsb * nsb : 1;
+  if (nseg == 1 && nnzb <= SMALL_MAX) {
+    // one segment: mode 1 with a single super-block has m = 1, so its budget is tau^2 too
+    { ++g_launches; k_trunc_small<<<1, SMALL_THREADS, 0, st>>>(x.brow, x.bcol, x.slot, n2, (int)nnzb, nb, tau * tau, keep); }
+    return cudaGetLastError();
+  }
   Work w = carve(work, nnzb, nseg, nsb);
   cudaError_t e;
   if (mode == 1) {

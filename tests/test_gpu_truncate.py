@@ -69,3 +69,17 @@ def test_device_input_matches_host_input():
     kd = sp2.sp2_truncate(T, 1e-4, "frobinf", 128).cpu().numpy()
     kh = sp2.sp2_truncate(X, 1e-4, "frobinf", 128)
     assert np.array_equal(kd, kh)
+
+
+@pytest.mark.parametrize("n", [2016, 2048, 2017])
+@pytest.mark.parametrize("mode", ["frobenius", "frobinf"])
+@pytest.mark.parametrize("tau", [0.0, 1e-4, 0.3])
+def test_keep_flags_around_one_cta_limit(n, mode, tau):
+    """2016 upper tiles (nb = 63) take the one-CTA select, 2080 (nb = 64, also
+    with a ragged tail) the multi-launch passes; both match the oracle bit for bit."""
+    import paper_1909_12533_gb300 as sp2
+    X = _decaying(n, 5, ties=True)
+    X.val[11] = 0.0
+    g = sp2.sp2_truncate(X, tau, mode, 4096)
+    o = _oracle_keep(X, tau, mode, 4096)
+    assert np.array_equal(g, o), np.nonzero(g != o)
