@@ -1,0 +1,168 @@
+// Measurement program (not part of libsp2): the rate at which 8 KB
+// cp.async.bulk copies can fill a ring of shared-memory stages, one CTA per SM,
+// one producer thread, one consumer thread that only releases each stage (no
+// compute).  This is the supply ceiling for the operand slices of the
+// tensor-core square, which streams 8 KB units the same way.  Every wait is
+// bounded (2 s) and reported through the error word.
+// Build and run: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o tma_supply tma_supply.cu && ./tma_supply
+#include <cstdio>
+#include <cstdint>
+#include <vector>
+#include <cuda_runtime.h>
+
+constexpr int UNIT = 8192;
+constexpr int MAXU = 4;
+constexpr int MAXST = 6;
+constexpr unsigned long long WAIT_NS = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+__device__ __forceinline__ unsigned long long now_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ bool try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ bool wait(uint64_t* bar, uint32_t parity) {
+  if (try_wait(bar, parity)) return true;
+  const unsigned long long t0 = now_ns();
+  while (!try_wait(bar, parity))
+    if (now_ns() - t0 > WAIT_NS) return false;
+  return true;
+}
+__device__ __forceinline__ uint32_t hash(uint32_t x) {
+  x ^= x >> 16; x *= 0x7feb352dU; x ^= x >> 15; x *= 0x846ca68bU; x ^= x >> 16;
+  return x;
+}
+
+// mode 0: units drawn per CTA; mode 1: the same unit sequence on every CTA
+__global__ void __launch_bounds__(64, 1) k_tma(const char* __restrict__ src, uint32_t nunits, int steps, int nst,
+                                               int units, int mode, long long* out, int* err) {
+  extern __shared__ __align__(1024) unsigned char stage[];
+  __shared__ uint64_t full[MAXST], empty[MAXST];
+  __shared__ long long t_issue[MAXST];
+  __shared__ volatile int issued, stop;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAXST; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    issued = 0;
+    stop = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    // producer
+    for (int step = 0; step < steps; ++step) {
+      const int s = step % nst;
+      const uint32_t par = ((step / nst) & 1) ^ 1;
+      if (stop || !wait(&empty[s], par)) { atomicOr(err, 1); stop = 1; break; }
+      t_issue[s] = clock64();   // before the arrive (release), read after the phase completes
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
+                   "r"((uint32_t)(units * UNIT))
+                   : "memory");
+      for (int u = 0; u < units; ++u) {
+        const uint32_t key = mode == 0 ? (blockIdx.x * 0x9E3779B9u) ^ (uint32_t)(step * MAXU + u)
+                                       : (uint32_t)(step * MAXU + u);
+        const uint32_t idx = hash(key) % nunits;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                smem_u32(stage + (s * MAXU + u) * UNIT)),
+            "l"(src + (size_t)idx * UNIT), "r"((uint32_t)UNIT), "r"(smem_u32(&full[s]))
+            : "memory");
+      }
+      issued = step + 1;
+    }
+  } else if (threadIdx.x == 32) {
+    // consumer: wait for the stage, release it
+    const long long t0 = clock64();
+    long long lat = 0;
+    int done = 0;
+    for (int step = 0; step < steps; ++step) {
+      const int s = step % nst;
+      const uint32_t par = (step / nst) & 1;
+      if (!wait(&full[s], par)) { atomicOr(err, 2); stop = 1; break; }
+      lat += clock64() - t_issue[s];
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
+      ++done;
+    }
+    const long long t1 = clock64();
+    if (done < steps) {
+      // copies still in flight: wait for them (bounded) before the CTA exits
+      const int last = issued;
+      for (int step = done; step < last; ++step)
+        if (!wait(&full[step % nst], (step / nst) & 1)) atomicOr(err, 4);
+    }
+    out[blockIdx.x * 2] = t1 - t0;
+    out[blockIdx.x * 2 + 1] = done ? lat / done : 0;
+  }
+}
+
+int main() {
+  int dev = 0, nsm = 0;
+  cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+  const size_t big = 4ull << 30;
+  char* buf = nullptr;
+  if (cudaMalloc(&buf, big) != cudaSuccess) { printf("alloc failed\n"); return 1; }
+  cudaMemset(buf, 1, big);
+  long long* out;
+  int* err;
+  cudaMalloc(&out, nsm * 2 * sizeof(long long));
+  cudaMalloc(&err, 4);
+  const int smem = MAXST * MAXU * UNIT;
+  cudaFuncSetAttribute(k_tma, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  struct V { const char* name; size_t bytes; int nst, units, mode; };
+  std::vector<V> vs = {
+      {"L2 64MB, per-CTA units, 6 stages x 4 units", 64ull << 20, 6, 4, 0},
+      {"L2 64MB, per-CTA units, 6 stages x 3 units", 64ull << 20, 6, 3, 0},
+      {"L2 64MB, per-CTA units, 3 stages x 4 units", 64ull << 20, 3, 4, 0},
+      {"L2 64MB, same units on all CTAs, 6 x 4", 64ull << 20, 6, 4, 1},
+      {"L2 16MB, per-CTA units, 6 x 4", 16ull << 20, 6, 4, 0},
+      {"DRAM 4GB, per-CTA units, 6 x 4", big, 6, 4, 0},
+  };
+  const int steps = 4000;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  for (const V& v : vs) {
+    const uint32_t nunits = (uint32_t)(v.bytes / UNIT);
+    float best = 1e30f;
+    double bpc = 0, lat = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaMemset(err, 0, 4);
+      cudaEventRecord(e0);
+      k_tma<<<nsm, 64, smem>>>(buf, nunits, steps, v.nst, v.units, v.mode, out, err);
+      cudaEventRecord(e1);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      int herr = 0;
+      cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+      if (ce != cudaSuccess || herr) { printf("%s: cuda %d err %d\n", v.name, (int)ce, herr); return 2; }
+      float ms;
+      cudaEventElapsedTime(&ms, e0, e1);
+      std::vector<long long> h(nsm * 2);
+      cudaMemcpy(h.data(), out, h.size() * 8, cudaMemcpyDeviceToHost);
+      double cyc = 0, l = 0;
+      for (int i = 0; i < nsm; ++i) { cyc += h[2 * i]; l += h[2 * i + 1]; }
+      cyc /= nsm;
+      l /= nsm;
+      if (ms < best) {
+        best = ms;
+        bpc = (double)steps * v.units * UNIT / cyc;
+        lat = l;
+      }
+    }
+    const double tbs = (double)nsm * steps * v.units * UNIT / (best * 1e-3) / 1e12;
+    printf("%-48s %.3f ms  %.2f TB/s  %.1f B/cycle/SM  issue->ready %.0f cycles\n", v.name, best, tbs, bpc, lat);
+  }
+  return 0;
+}
