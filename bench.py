@@ -349,7 +349,10 @@ def main(argv=None) -> int:
                 "note": "achieved/frac count algorithmic flops (2*32^3 per tile triplet); hw_* count the "
                         "FP16 MMAs issued (slice pairs s + t <= %d, pairs that multiply an all-zero panel "
                         "slice skipped, 128x128 super-tile padding included); traffic = DRAM bytes per launch "
-                        "from ncu, null when the kernel source differs from the captured one"
+                        "from ncu, null when the kernel source differs from the captured one; the binding limit "
+                        "is the supply of operand slices into shared memory (ncu on the water-like N=9600 "
+                        "case: 6.9 TB/s of L2-to-SM reads, 86%% of the 8.0 TB/s that 8 KB bulk copies reach "
+                        "with no compute), not the tensor pipe"
                         % (args.slices - 1),
                 "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured; FP16 = BF16 rate)"}
     line = {
