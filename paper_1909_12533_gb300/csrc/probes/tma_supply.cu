@@ -108,6 +108,99 @@ __global__ void __launch_bounds__(64, 1) k_tma(const char* __restrict__ src, uin
   }
 }
 
+// Same ring in 2-CTA clusters: CTA r issues the units u = r (mod 2) of every
+// stage with .multicast::cluster to both CTAs, so each unit is read once from
+// L2 and lands in both shared memories.  A stage is reused once both consumers
+// have released it (each consumer arrives on its own and the peer's empty
+// barrier).  Both CTAs always reach the final cluster barrier.
+__global__ void __launch_bounds__(64, 1) k_tma_mc(const char* __restrict__ src, uint32_t nunits, int steps, int nst,
+                                                  int units, long long* out, int* err) {
+  extern __shared__ __align__(1024) unsigned char stage[];
+  __shared__ uint64_t full[MAXST], empty[MAXST];
+  __shared__ long long t_issue[MAXST];
+  __shared__ volatile int issued, stop;
+  uint32_t rank;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(rank));
+  const uint32_t peer = rank ^ 1u;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAXST; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 2;" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    issued = 0;
+    stop = 0;
+  }
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+  const uint32_t cid = blockIdx.x >> 1;
+  if (threadIdx.x == 0) {
+    for (int step = 0; step < steps; ++step) {
+      const int s = step % nst;
+      const uint32_t par = ((step / nst) & 1) ^ 1;
+      if (stop || !wait(&empty[s], par)) { atomicOr(err, 1); stop = 1; break; }
+      t_issue[s] = clock64();
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
+                   "r"((uint32_t)(units * UNIT))
+                   : "memory");
+      for (int u = (int)rank; u < units; u += 2) {
+        const uint32_t idx = hash((cid * 0x9E3779B9u) ^ (uint32_t)(step * MAXU + u)) % nunits;
+        asm volatile(
+            "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.multicast::cluster [%0], [%1], %2, "
+            "[%3], %4;" ::"r"(smem_u32(stage + (s * MAXU + u) * UNIT)),
+            "l"(src + (size_t)idx * UNIT), "r"((uint32_t)UNIT), "r"(smem_u32(&full[s])), "h"((uint16_t)3)
+            : "memory");
+      }
+      issued = step + 1;
+    }
+  } else if (threadIdx.x == 32) {
+    const long long t0 = clock64();
+    long long lat = 0;
+    int done = 0;
+    for (int step = 0; step < steps; ++step) {
+      const int s = step % nst;
+      const uint32_t par = (step / nst) & 1;
+      if (!wait(&full[s], par)) { atomicOr(err, 2); stop = 1; break; }
+      lat += clock64() - t_issue[s];
+      uint32_t remote;
+      asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(remote) : "r"(smem_u32(&empty[s])), "r"(peer));
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
+      asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(remote) : "memory");
+      ++done;
+    }
+    const long long t1 = clock64();
+    if (done < steps) {
+      const int last = issued;
+      for (int step = done; step < last; ++step)
+        if (!wait(&full[step % nst], (step / nst) & 1)) atomicOr(err, 4);
+    }
+    out[blockIdx.x * 2] = t1 - t0;
+    out[blockIdx.x * 2 + 1] = done ? lat / done : 0;
+  }
+  __syncwarp();
+  __syncthreads();
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// Reference point: the same 8 KB units read by plain coalesced 16-byte loads
+// into registers (L1 bypassed), 32 warps per SM, one unit per warp per
+// iteration; the loaded words are folded into a value that is stored only if
+// it takes an impossible value.
+__global__ void __launch_bounds__(1024, 1) k_ldg(const uint4* __restrict__ src, uint32_t nunits, int iters,
+                                                 uint4* sink) {
+  const uint32_t warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  uint4 acc = make_uint4(0u, 0u, 0u, 0u);
+  for (int it = 0; it < iters; ++it) {
+    const uint32_t idx = hash((blockIdx.x * 0x9E3779B9u) ^ (uint32_t)(it * 32 + (int)warp)) % nunits;
+    const uint4* u = src + (size_t)idx * (UNIT / 16);
+#pragma unroll
+    for (int k = 0; k < UNIT / 512; ++k) {
+      const uint4 v = __ldcg(u + k * 32 + lane);
+      acc.x ^= v.x; acc.y ^= v.y; acc.z ^= v.z; acc.w ^= v.w;
+    }
+  }
+  if (acc.x == 0x9E3779B9u && acc.y == 0x7feb352du) sink[blockIdx.x * blockDim.x + threadIdx.x] = acc;
+}
+
 int main() {
   int dev = 0, nsm = 0;
   cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
@@ -163,6 +256,78 @@ int main() {
     }
     const double tbs = (double)nsm * steps * v.units * UNIT / (best * 1e-3) / 1e12;
     printf("%-48s %.3f ms  %.2f TB/s  %.1f B/cycle/SM  issue->ready %.0f cycles\n", v.name, best, tbs, bpc, lat);
+  }
+  {
+    // plain loads into registers
+    uint4* sink;
+    cudaMalloc(&sink, (size_t)nsm * 1024 * 16);
+    const uint32_t nunits = (uint32_t)((64ull << 20) / UNIT);
+    const int iters = 200;
+    float best = 1e30f;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaEventRecord(e0);
+      k_ldg<<<nsm, 1024>>>(reinterpret_cast<const uint4*>(buf), nunits, iters, sink);
+      cudaEventRecord(e1);
+      if (cudaEventSynchronize(e1) != cudaSuccess) { printf("ldg failed\n"); return 2; }
+      float ms;
+      cudaEventElapsedTime(&ms, e0, e1);
+      best = ms < best ? ms : best;
+    }
+    int clk_khz = 0;
+    cudaDeviceGetAttribute(&clk_khz, cudaDevAttrClockRate, dev);
+    const double bytes = (double)nsm * 32 * iters * UNIT;
+    printf("L2 64MB, plain 16-byte loads (L1 bypassed), 32 warps/SM     %.3f ms  %.2f TB/s  ~%.1f B/cycle/SM at %d MHz\n",
+           best, bytes / (best * 1e-3) / 1e12, bytes / nsm / (best * 1e-3) / (clk_khz * 1e3), clk_khz / 1000);
+    cudaFree(sink);
+  }
+  // 2-CTA clusters with multicast: bytes landed per SM (each unit read once for two SMs)
+  cudaFuncSetAttribute(k_tma_mc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  for (int units : {4, 2}) {
+    const uint32_t nunits = (uint32_t)((64ull << 20) / UNIT);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(nsm & ~1);
+    cfg.blockDim = dim3(64);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = 2;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    float best = 1e30f;
+    double bpc = 0, lat = 0;
+    for (int rep = 0; rep < 3; ++rep) {
+      cudaMemset(err, 0, 4);
+      cudaEventRecord(e0);
+      cudaError_t le = cudaLaunchKernelEx(&cfg, k_tma_mc, (const char*)buf, nunits, steps, 6, units, out, err);
+      cudaEventRecord(e1);
+      cudaError_t ce = cudaEventSynchronize(e1);
+      int herr = 0;
+      cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+      if (le != cudaSuccess || ce != cudaSuccess || herr) {
+        printf("multicast %d units: launch %d cuda %d err %d\n", units, (int)le, (int)ce, herr);
+        return 2;
+      }
+      float ms;
+      cudaEventElapsedTime(&ms, e0, e1);
+      const int g = nsm & ~1;
+      std::vector<long long> h(g * 2);
+      cudaMemcpy(h.data(), out, h.size() * 8, cudaMemcpyDeviceToHost);
+      double cyc = 0, l = 0;
+      for (int i = 0; i < g; ++i) { cyc += h[2 * i]; l += h[2 * i + 1]; }
+      cyc /= g;
+      l /= g;
+      if (ms < best) {
+        best = ms;
+        bpc = (double)steps * units * UNIT / cyc;
+        lat = l;
+      }
+    }
+    const int g = nsm & ~1;
+    const double landed = (double)g * steps * units * UNIT / (best * 1e-3) / 1e12;
+    printf("L2 64MB, 2-CTA multicast, 6 stages x %d units          %.3f ms  landed %.2f TB/s (L2 reads %.2f)  "
+           "%.1f B/cycle/SM  issue->ready %.0f cycles\n", units, best, landed, landed / 2, bpc, lat);
   }
   return 0;
 }
