@@ -4,10 +4,11 @@
 // compute).  This is the supply ceiling for the operand slices of the
 // tensor-core square, which streams 8 KB units the same way.  Every wait is
 // bounded (2 s) and reported through the error word.
-// Build and run: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o tma_supply tma_supply.cu && ./tma_supply
+// Build and run: nvcc -gencode arch=compute_103a,code=sm_103a -O3 -o tma_supply tma_supply.cu -lcuda && ./tma_supply
 #include <cstdio>
 #include <cstdint>
 #include <vector>
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 constexpr int UNIT = 8192;
@@ -181,6 +182,67 @@ __global__ void __launch_bounds__(64, 1) k_tma_mc(const char* __restrict__ src, 
   asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
 }
 
+// The same ring fed by tiled tensor-map copies: the buffer seen as rows of
+// 64 16-bit elements (128 B), one 64 x 64 box (8 KB) per unit, x = 0.
+__global__ void __launch_bounds__(64, 1) k_tma_2d(const __grid_constant__ CUtensorMap tmap, uint32_t nunits, int steps,
+                                                  int nst, int units, long long* out, int* err) {
+  extern __shared__ __align__(1024) unsigned char stage[];
+  __shared__ uint64_t full[MAXST], empty[MAXST];
+  __shared__ long long t_issue[MAXST];
+  __shared__ volatile int issued, stop;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAXST; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    issued = 0;
+    stop = 0;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int step = 0; step < steps; ++step) {
+      const int s = step % nst;
+      const uint32_t par = ((step / nst) & 1) ^ 1;
+      if (stop || !wait(&empty[s], par)) { atomicOr(err, 1); stop = 1; break; }
+      t_issue[s] = clock64();
+      asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(&full[s])),
+                   "r"((uint32_t)(units * UNIT))
+                   : "memory");
+      for (int u = 0; u < units; ++u) {
+        const uint32_t idx = hash((blockIdx.x * 0x9E3779B9u) ^ (uint32_t)(step * MAXU + u)) % nunits;
+        const int x = 0, y = (int)(idx * 64u);
+        asm volatile(
+            "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];"
+            ::"r"(smem_u32(stage + (s * MAXU + u) * UNIT)), "l"(reinterpret_cast<uint64_t>(&tmap)), "r"(x), "r"(y),
+            "r"(smem_u32(&full[s]))
+            : "memory");
+      }
+      issued = step + 1;
+    }
+  } else if (threadIdx.x == 32) {
+    const long long t0 = clock64();
+    long long lat = 0;
+    int done = 0;
+    for (int step = 0; step < steps; ++step) {
+      const int s = step % nst;
+      const uint32_t par = (step / nst) & 1;
+      if (!wait(&full[s], par)) { atomicOr(err, 2); stop = 1; break; }
+      lat += clock64() - t_issue[s];
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
+      ++done;
+    }
+    const long long t1 = clock64();
+    if (done < steps) {
+      const int last = issued;
+      for (int step = done; step < last; ++step)
+        if (!wait(&full[step % nst], (step / nst) & 1)) atomicOr(err, 4);
+    }
+    out[blockIdx.x * 2] = t1 - t0;
+    out[blockIdx.x * 2 + 1] = done ? lat / done : 0;
+  }
+}
+
 // Reference point: the same 8 KB units read by plain coalesced 16-byte loads
 // into registers (L1 bypassed), 32 warps per SM, one unit per warp per
 // iteration; the loaded words are folded into a value that is stored only if
@@ -279,6 +341,53 @@ int main() {
     printf("L2 64MB, plain 16-byte loads (L1 bypassed), 32 warps/SM     %.3f ms  %.2f TB/s  ~%.1f B/cycle/SM at %d MHz\n",
            best, bytes / (best * 1e-3) / 1e12, bytes / nsm / (best * 1e-3) / (clk_khz * 1e3), clk_khz / 1000);
     cudaFree(sink);
+  }
+  {
+    // tiled tensor-map copies, 64 MB buffer as rows of 128 B
+    const uint64_t rows = (64ull << 20) / 128;
+    CUtensorMap tmap;
+    const cuuint64_t dims[2] = {64, rows};
+    const cuuint64_t strides[1] = {128};
+    const cuuint32_t box[2] = {64, 64};
+    const cuuint32_t estr[2] = {1, 1};
+    const CUresult r = cuTensorMapEncodeTiled(&tmap, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, buf, dims, strides, box, estr,
+                                              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                                              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+      printf("tensor map encode failed: %d\n", (int)r);
+    } else {
+      cudaFuncSetAttribute(k_tma_2d, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+      const uint32_t nunits = (uint32_t)((64ull << 20) / UNIT);
+      for (int nst : {6, 3}) {
+        float best = 1e30f;
+        double bpc = 0, lat = 0;
+        for (int rep = 0; rep < 3; ++rep) {
+          cudaMemset(err, 0, 4);
+          cudaEventRecord(e0);
+          k_tma_2d<<<nsm, 64, smem>>>(tmap, nunits, steps, nst, 4, out, err);
+          cudaEventRecord(e1);
+          cudaError_t ce = cudaEventSynchronize(e1);
+          int herr = 0;
+          cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+          if (ce != cudaSuccess || herr) { printf("tensor copies: cuda %d err %d\n", (int)ce, herr); return 2; }
+          float ms;
+          cudaEventElapsedTime(&ms, e0, e1);
+          std::vector<long long> h(nsm * 2);
+          cudaMemcpy(h.data(), out, h.size() * 8, cudaMemcpyDeviceToHost);
+          double cyc = 0, l = 0;
+          for (int i = 0; i < nsm; ++i) { cyc += h[2 * i]; l += h[2 * i + 1]; }
+          cyc /= nsm;
+          l /= nsm;
+          if (ms < best) {
+            best = ms;
+            bpc = (double)steps * 4 * UNIT / cyc;
+            lat = l;
+          }
+        }
+        printf("L2 64MB, tensor-map 64x64 boxes, %d stages x 4 units            %.3f ms  %.2f TB/s  %.1f B/cycle/SM  "
+               "issue->ready %.0f cycles\n", nst, best, (double)nsm * steps * 4 * UNIT / (best * 1e-3) / 1e12, bpc, lat);
+      }
+    }
   }
   // 2-CTA clusters with multicast: bytes landed per SM (each unit read once for two SMs)
   cudaFuncSetAttribute(k_tma_mc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
