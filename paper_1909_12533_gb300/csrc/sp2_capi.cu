@@ -18,7 +18,7 @@
 using namespace sp2;
 
 namespace sp2 {
-long long g_launches = 0;
+thread_local long long g_launches = 0;
 }
 
 namespace {

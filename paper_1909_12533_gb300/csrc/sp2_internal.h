@@ -38,7 +38,7 @@ struct FullPattern {
 constexpr uint32_t REF_T = 0x80000000u;
 
 // Host-side count of the kernels this library has launched (reported per run).
-extern long long g_launches;
+extern thread_local long long g_launches;   // launches issued by this host thread
 
 // Per-output-tile partial sums written by the fused epilogue.
 struct Partials {
