@@ -243,6 +243,96 @@ __global__ void __launch_bounds__(64, 1) k_tma_2d(const __grid_constant__ CUtens
   }
 }
 
+// The same ring filled by 16-byte cp.async from W copy warps (warp w copies
+// the units u = w (mod W) of each stage, 16 bytes per lane per 512), each lane
+// arriving on the stage's barrier once its copies have landed; the last warp's
+// lane 0 consumes.  Every wait is bounded.
+template <int W>
+__global__ void __launch_bounds__(32 * (W + 1), 1) k_cpasync(const char* __restrict__ src, uint32_t nunits,
+                                                            int steps, int nst, int units, long long* out, int* err) {
+  extern __shared__ __align__(1024) unsigned char stage[];
+  __shared__ uint64_t full[MAXST], empty[MAXST];
+  __shared__ volatile int stop;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < MAXST; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&full[s])), "r"(32 * W) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])) : "memory");
+    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    stop = 0;
+  }
+  __syncthreads();
+  if (warp < W) {
+    for (int step = 0; step < steps; ++step) {
+      const int s = step % nst;
+      const uint32_t par = ((step / nst) & 1) ^ 1;
+      int good = 1;
+      if (lane == 0) good = (!stop && wait(&empty[s], par)) ? 1 : 0;
+      good = __shfl_sync(0xffffffffu, good, 0);
+      if (!good) {
+        if (lane == 0) { atomicOr(err, 1); stop = 1; }
+        break;
+      }
+      for (int u = warp; u < units; u += W) {
+        const uint32_t idx = hash((blockIdx.x * 0x9E3779B9u) ^ (uint32_t)(step * MAXU + u)) % nunits;
+        const char* g = src + (size_t)idx * UNIT + 16 * lane;
+        const uint32_t d = smem_u32(stage + (s * MAXU + u) * UNIT) + 16u * (uint32_t)lane;
+#pragma unroll
+        for (int k = 0; k < UNIT / 512; ++k)
+          asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + 512u * k), "l"(g + 512 * k) : "memory");
+      }
+      asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[s])) : "memory");
+    }
+    asm volatile("cp.async.wait_all;" ::: "memory");
+  } else if (lane == 0) {
+    const long long t0 = clock64();
+    int done = 0;
+    for (int step = 0; step < steps; ++step) {
+      const int s = step % nst;
+      const uint32_t par = (step / nst) & 1;
+      if (!wait(&full[s], par)) { atomicOr(err, 2); stop = 1; break; }
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&empty[s])) : "memory");
+      ++done;
+    }
+    out[blockIdx.x * 2] = clock64() - t0;
+    out[blockIdx.x * 2 + 1] = done;
+  }
+}
+
+template <int W>
+int run_cpasync(const char* buf, int nsm, int steps, int smem, long long* out, int* err, cudaEvent_t e0,
+                cudaEvent_t e1) {
+  cudaFuncSetAttribute(k_cpasync<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  const uint32_t nunits = (uint32_t)((64ull << 20) / UNIT);
+  float best = 1e30f;
+  double bpc = 0;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaMemset(err, 0, 4);
+    cudaEventRecord(e0);
+    k_cpasync<W><<<nsm, 32 * (W + 1), smem>>>(buf, nunits, steps, 6, 4, out, err);
+    cudaEventRecord(e1);
+    cudaError_t ce = cudaEventSynchronize(e1);
+    int herr = 0;
+    cudaMemcpy(&herr, err, 4, cudaMemcpyDeviceToHost);
+    if (ce != cudaSuccess || herr) { printf("cp.async %d warps: cuda %d err %d\n", W, (int)ce, herr); return 2; }
+    float ms;
+    cudaEventElapsedTime(&ms, e0, e1);
+    std::vector<long long> h(nsm * 2);
+    cudaMemcpy(h.data(), out, h.size() * 8, cudaMemcpyDeviceToHost);
+    double cyc = 0;
+    for (int i = 0; i < nsm; ++i) cyc += h[2 * i];
+    cyc /= nsm;
+    if (ms < best) {
+      best = ms;
+      bpc = (double)steps * 4 * UNIT / cyc;
+    }
+  }
+  printf("L2 64MB, 16-byte cp.async from %d warp(s), 6 stages x 4 units   %.3f ms  %.2f TB/s  %.1f B/cycle/SM\n", W,
+         best, (double)nsm * steps * 4 * UNIT / (best * 1e-3) / 1e12, bpc);
+  return 0;
+}
+
 // Reference point: the same 8 KB units read by plain coalesced 16-byte loads
 // into registers (L1 bypassed), 32 warps per SM, one unit per warp per
 // iteration; the loaded words are folded into a value that is stored only if
@@ -389,6 +479,9 @@ int main() {
       }
     }
   }
+  if (run_cpasync<1>(buf, nsm, steps, smem, out, err, e0, e1) || run_cpasync<2>(buf, nsm, steps, smem, out, err, e0, e1) ||
+      run_cpasync<4>(buf, nsm, steps, smem, out, err, e0, e1))
+    return 2;
   // 2-CTA clusters with multicast: bytes landed per SM (each unit read once for two SMs)
   cudaFuncSetAttribute(k_tma_mc, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   for (int units : {4, 2}) {
