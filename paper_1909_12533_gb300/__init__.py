@@ -429,7 +429,14 @@ def _autograd_function():
     return SP2Function
 
 
+_SP2_FUNCTION = None
+
+
 def __getattr__(name):
+    # built on first use (imports torch), then the same class every time
+    global _SP2_FUNCTION
     if name == "SP2Function":
-        return _autograd_function()
+        if _SP2_FUNCTION is None:
+            _SP2_FUNCTION = _autograd_function()
+        return _SP2_FUNCTION
     raise AttributeError(name)
