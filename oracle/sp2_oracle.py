@@ -296,14 +296,15 @@ def apply_drop(X: np.ndarray, dropped, b: int = B) -> np.ndarray:
 
 
 def product_pattern(kept, nb: int) -> set:
-    """Tile pattern of X~^2 on the upper triangle, united with the diagonal:
-    (I, J), I <= J, is present iff some K has X~_IK != 0 and X~_KJ != 0 as
-    stored tiles (integer work, the exact boolean product)."""
+    """Tile pattern of X_i = c0 I + c1 X~ + c2 X~^2 (Algorithm 2) on the upper
+    triangle: (I, J), I <= J, is present iff some K has X~_IK and X~_KJ stored
+    (the product X~^2), or X~_IJ itself is stored (the c1 X~ term), or I = J
+    (the c0 I term).  Integer work, the exact boolean product."""
     A = np.zeros((nb, nb), dtype=np.int64)
     for i, j in kept:
         A[i, j] = 1
         A[j, i] = 1
-    P = (A @ A) > 0
+    P = ((A @ A) > 0) | (A > 0)
     np.fill_diagonal(P, True)
     iu, ju = np.nonzero(np.triu(P))
     return set(zip(iu.tolist(), ju.tolist()))

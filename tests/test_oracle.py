@@ -242,6 +242,97 @@ def test_banded_matrix_norm_experiment(permute):
             assert MM < 0.6 * fro    # Frob-Inf already well below Frobenius at N = 3000
 
 
+# ----------------------------------------------------------------- symbolic square
+def _random_kept(rng, nb, density, drop_diag=()):
+    """A random upper tile pattern (sorted (I, J) list) with the given diagonal
+    tiles left out."""
+    kept = []
+    for i in range(nb):
+        for j in range(i, nb):
+            if i == j:
+                if i not in drop_diag:
+                    kept.append((i, j))
+            elif rng.random() < density:
+                kept.append((i, j))
+    return kept
+
+
+# hand-made cases next to random ones: an isolated coupling (0, 1) with both
+# diagonal tiles gone and no K joining them, a chain, a single tile
+_HAND = [
+    (4, [(0, 1), (2, 2), (2, 3), (3, 3)]),
+    (5, [(0, 1), (1, 2), (2, 3), (3, 4)]),
+    (3, [(1, 1)]),
+    (1, [(0, 0)]),
+]
+
+
+@pytest.mark.parametrize("case", range(len(_HAND) + 6))
+def test_triplet_count_brute_force(case):
+    # the headline's numerator: (I <= J, K) with X~_IK and X~_KJ stored (either
+    # triangle), counted by an explicit triple loop
+    if case < len(_HAND):
+        nb, kept = _HAND[case]
+    else:
+        rng = np.random.default_rng(100 + case)
+        nb = int(rng.integers(2, 9))
+        kept = _random_kept(rng, nb, rng.uniform(0.1, 0.9), drop_diag=set(rng.integers(0, nb, 2).tolist()))
+    stored = set(kept) | {(j, i) for i, j in kept}
+    brute = sum(1 for i in range(nb) for j in range(i, nb) for k in range(nb)
+                if (i, k) in stored and (k, j) in stored)
+    assert O._triplets(kept, nb) == brute
+
+
+@pytest.mark.parametrize("case", range(len(_HAND) + 6))
+def test_product_pattern_matches_nonzero_tiles_of_the_polynomial(case):
+    # the tile pattern of X_i = c0 I + c1 X~ + c2 X~^2 (Algorithm 2), found from
+    # the arithmetic itself: positive values on the stored tiles and positive
+    # coefficients, so no tile cancels
+    if case < len(_HAND):
+        nb, kept = _HAND[case]
+    else:
+        rng = np.random.default_rng(200 + case)
+        nb = int(rng.integers(2, 9))
+        kept = _random_kept(rng, nb, rng.uniform(0.1, 0.9), drop_diag=set(rng.integers(0, nb, 2).tolist()))
+    rng = np.random.default_rng(case)
+    b = 4                      # small tiles: the pattern does not depend on the tile size
+    X = np.zeros((nb * b, nb * b))
+    for i, j in kept:
+        blk = rng.uniform(0.5, 1.0, (b, b))
+        X[i * b:(i + 1) * b, j * b:(j + 1) * b] = blk
+        X[j * b:(j + 1) * b, i * b:(i + 1) * b] = blk.T
+    Xi = 0.3 * np.eye(nb * b) + 0.7 * X + 1.1 * (X @ X)
+    nz = {(i, j) for i in range(nb) for j in range(i, nb)
+          if np.any(Xi[i * b:(i + 1) * b, j * b:(j + 1) * b] != 0.0)}
+    assert O.product_pattern(kept, nb) == nz
+    if case == 0:
+        assert (0, 1) in nz    # kept only through the c1 X~ term
+
+
+@pytest.mark.parametrize("seed", range(8))
+def test_truncation_of_a_psd_matrix_never_isolates_a_coupling_tile(seed):
+    # For X >= 0, ||X_IJ||_F <= sqrt(||X_II||_F ||X_JJ||_F) (Hoelder), so the
+    # ascending prefix that drops both diagonal tiles of a pair also drops their
+    # coupling: the case pattern(X~) not in pattern(X~^2) cannot come out of the
+    # Frobenius selection on the (positive semidefinite) iterates.
+    rng = np.random.default_rng(seed)
+    nb = 4
+    n = nb * 32
+    Y = rng.standard_normal((n, 6)) * np.repeat(10.0 ** rng.uniform(-4, 0, nb), 32)[:, None]
+    X = Y @ Y.T
+    _, tiles = O.upper_tiles(X)
+    n2 = {(i, j): v for i, j, v in tiles}
+    for i in range(nb):
+        for j in range(i + 1, nb):
+            assert math.sqrt(n2[(i, j)]) <= (n2[(i, i)] * n2[(j, j)]) ** 0.25 * (1 + 1e-12)
+    for tau in 10.0 ** np.linspace(-8, 1, 40):
+        _, kept, _ = O.truncate_select(X, tau, "frobenius")
+        ks = set(kept)
+        for i, j in kept:
+            if i != j:
+                assert (i, i) in ks or (j, j) in ks
+
+
 # ----------------------------------------------------------------- Algorithms 1 + 2
 def test_sp2_tau0_matches_eigendecomposition_projector():
     c = make_config(1)
