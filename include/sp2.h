@@ -51,6 +51,9 @@ extern "C" {
 #define SP2_ERR_STATE         -9  /* call out of order (e.g. get_D before run)     */
 #define SP2_ERR_CAPACITY     -10  /* caller buffer too small (size returned)       */
 #define SP2_ERR_TOO_LARGE    -11  /* input exceeds the fixed scratch of sp2_truncate_noalloc */
+#define SP2_ERR_RANGE        -12  /* an iterate left the range of the method: an element with |x| >= 2
+                                     met the tensor-core slicing, or e_i / t_i is not finite
+                                     (homo/lumo bounds that do not bracket the gap, or divergence) */
 
 #define SP2_TILE 32
 #define SP2_MAX_ITER 128
@@ -117,6 +120,16 @@ typedef struct {
                               K tiles adds its FP32 tensor-memory sums into the exact fixed-point
                               total every 16 K tiles (keeps the sums exact for dense operands);
                               0 = never; default 512                                    */
+  int32_t wait_limit_ms;   /* every bounded wait inside a tensor-core kernel gives up after this
+                              many milliseconds with SP2_ERR_TIMEOUT; default 2000      */
+  int32_t selftest;        /* tests of the error paths (no fault, no data touched); default 0.
+                              1: in the first sp2_run of the context the first tensor-core square
+                              waits, before it moves any data, on a barrier that nothing arrives
+                              at; the wait gives up after wait_limit_ms and sp2_run returns
+                              SP2_ERR_TIMEOUT.  2: in the first sp2_run the first slicing of a
+                              tensor-core operand reports an out-of-range element (its data are
+                              unchanged) and sp2_run returns SP2_ERR_RANGE.  Later runs of the
+                              context are unaffected.                                   */
 } sp2_params;
 
 typedef struct {
@@ -162,6 +175,19 @@ int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, d
                const sp2_params* params, const sp2_allocator* alloc, void* cuda_stream,
                sp2_ctx** out);
 
+/* sp2_create for a dense F (Section 1: F is the N x N Fock/Kohn-Sham matrix;
+ * Algorithm 1 takes it as it is).  F: n x n, row-major with leading dimension
+ * ld >= n (in doubles), host or device memory per on_device; it must be
+ * symmetric.  Only the tiles on and above the block diagonal are read (the
+ * 32 x 32 tiles (I, J), I <= J; the diagonal tiles in full); the tiles that
+ * are exactly zero are left out of the stored pattern, the diagonal tiles are
+ * always kept.  The dense matrix is tiled on the device (a temporary copy of F
+ * is made with the context's allocator when F is on the host); the caller
+ * keeps ownership of F.  Other arguments and errors as sp2_create. */
+int sp2_create_dense(const double* F, int64_t n, int64_t ld, int32_t on_device, int64_t nocc, double homo_ub,
+                     double lumo_lb, double tau, const sp2_params* params, const sp2_allocator* alloc,
+                     void* cuda_stream, sp2_ctx** out);
+
 /* Step 2 of Section 4 (Algorithm 2) and Step 3: iterate until the stop test
  * fires, then estimate homo/lumo.  Returns SP2_OK, SP2_ERR_NOT_CONVERGED (D is
  * the last iterate and readable), or an error.  stats may be NULL. */
@@ -176,6 +202,15 @@ int sp2_get_D(sp2_ctx* ctx, sp2_bsr* view);
  * and SP2_ERR_CAPACITY returned. */
 int sp2_copy_D(sp2_ctx* ctx, int32_t* brow, int32_t* bcol, double* val, int64_t cap_nnzb,
                int32_t on_device, int64_t* nnzb_out);
+
+/* D as a dense n x n matrix (both triangles; Section 1, Eq. (3): D is the
+ * projector onto the occupied subspace) written to out, row-major with leading
+ * dimension ld >= n (in doubles), host or device memory per on_device; the
+ * caller owns out.  The entries outside D's stored tiles are written as zero.
+ * The dense matrix is assembled on the device (a temporary n x n buffer from
+ * the context's allocator when out is on the host).  Synchronises the stream.
+ * Errors: INVALID_ARG, STATE (no D yet), OOM, CUDA. */
+int sp2_copy_D_dense(sp2_ctx* ctx, double* out, int64_t ld, int32_t on_device);
 
 /* Reverse-mode derivative of L = trace(D W) (not in the paper): W symmetric,
  * given on any tile pattern (only tiles of D's pattern matter).  Writes
@@ -209,15 +244,18 @@ int sp2_truncate(const sp2_bsr* X, double tau, int32_t mode, int64_t frobinf_par
  * dimension, nnzb the tile count, tiles sorted upper-triangle) and keep[nnzb]
  * for the result (1 = kept).  Work is queued on cuda_stream and not
  * synchronised.
- * Scratch: one file-scope device array of 8 MiB in this library, shared by all
- * calls on a device and kept by every GPU that loads the library until the
- * process exits.  Limits: nnzb <= 262144 tiles and, in Frob-Inf mode, at most
- * 32 x 32 super-blocks; larger inputs return SP2_ERR_TOO_LARGE.  The first call
- * on a device looks the array's device address up (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  The
- * array keeps the previous call's contents; everything that must start at zero
- * is cleared inside the call.  Calls that overlap on the GPU (different streams
- * or devices sharing the array) race on the scratch: serialise them.
+ * Scratch: one file-scope device array of 8 MiB in this library.  Every GPU
+ * that loads the library holds its own copy until the process exits, and all
+ * calls on that GPU share it.  Limits: nnzb <= 262144 tiles and, in Frob-Inf
+ * mode, at most 32 x 32 super-blocks (and the selection's work area must fit
+ * into the array); larger inputs return SP2_ERR_TOO_LARGE.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress) with that
+ * device current and keeps it; make that first call before any stream capture.
+ * A cudaDeviceReset of the device invalidates the kept address: do not call
+ * this entry point on a device after resetting it.  The array keeps the
+ * previous call's contents; everything that must start at zero is cleared
+ * inside the call.  Calls on the same device that overlap on the GPU (for
+ * example queued on two streams) race on that device's array: serialise them.
  * No cudaMalloc, cudaFree or other allocating routine is called.
  * Errors: INVALID_ARG, TOO_LARGE, CUDA. */
 int sp2_truncate_noalloc(const int32_t* brow, const int32_t* bcol, const double* val, int64_t n, int64_t nnzb,

@@ -24,7 +24,7 @@ SP2_OK = 0
 ERRORS = {
     -1: "SP2_ERR_INVALID_ARG", -2: "SP2_ERR_BOUNDS", -3: "SP2_ERR_PATTERN", -4: "SP2_ERR_NONFINITE",
     -5: "SP2_ERR_OOM", -6: "SP2_ERR_CUDA", -7: "SP2_ERR_NOT_CONVERGED", -8: "SP2_ERR_TIMEOUT",
-    -9: "SP2_ERR_STATE", -10: "SP2_ERR_CAPACITY", -11: "SP2_ERR_TOO_LARGE",
+    -9: "SP2_ERR_STATE", -10: "SP2_ERR_CAPACITY", -11: "SP2_ERR_TOO_LARGE", -12: "SP2_ERR_RANGE",
 }
 NOT_CONVERGED = -7
 MODES = {"sp2": 0, "sp2acc": 1}
@@ -47,7 +47,7 @@ class sp2_params(ctypes.Structure):
                 ("frobinf_part", c_int64), ("gamma", c_double), ("delta_acc", c_double), ("n_max_cap", c_int32),
                 ("precision", c_int32), ("slices", c_int32), ("mixed_from", c_int32), ("mixed_until", c_int32),
                 ("ckpt_every", c_int32), ("record_masks", c_int32), ("fp64_tail", c_double),
-                ("acc_flush_min", c_int32)]
+                ("acc_flush_min", c_int32), ("wait_limit_ms", c_int32), ("selftest", c_int32)]
 
 
 class sp2_stats(ctypes.Structure):
@@ -66,9 +66,12 @@ _SIGS = [
     ("sp2_default_params", c_int32, [POINTER(sp2_params)]),
     ("sp2_create", c_int32, [POINTER(sp2_bsr), c_int64, c_double, c_double, c_double, POINTER(sp2_params),
                              POINTER(sp2_allocator), c_void_p, POINTER(c_void_p)]),
+    ("sp2_create_dense", c_int32, [c_void_p, c_int64, c_int64, c_int32, c_int64, c_double, c_double, c_double,
+                                   POINTER(sp2_params), POINTER(sp2_allocator), c_void_p, POINTER(c_void_p)]),
     ("sp2_run", c_int32, [c_void_p, POINTER(sp2_stats)]),
     ("sp2_get_D", c_int32, [c_void_p, POINTER(sp2_bsr)]),
     ("sp2_copy_D", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, POINTER(c_int64)]),
+    ("sp2_copy_D_dense", c_int32, [c_void_p, c_void_p, c_int64, c_int32]),
     ("sp2_backward", c_int32, [c_void_p, POINTER(sp2_bsr), POINTER(sp2_bsr)]),
     ("sp2_truncate", c_int32, [POINTER(sp2_bsr), c_double, c_int32, c_int64, c_void_p, c_void_p]),
     ("sp2_truncate_noalloc", c_int32, [c_void_p, c_void_p, c_void_p, c_int64, c_int64, c_double, c_int32, c_int64,
@@ -173,15 +176,39 @@ def _stream_handle(stream):
     return c_void_p(0)
 
 
+def _is_dense(F) -> bool:
+    """A 2-D numpy array or torch tensor (dense F), as opposed to a tile set."""
+    shape = getattr(F, "shape", None)
+    return shape is not None and len(shape) == 2 and not hasattr(F, "brow")
+
+
 def sp2_create(F, nocc: int, homo_ub: float, lumo_lb: float, tau: float, params: sp2_params | None = None,
-               stream=None) -> c_void_p:
-    """F: object with n, brow, bcol, val (numpy -> host copy, CUDA tensors -> device copy)."""
-    bsr, keep = make_bsr(F.n, F.brow, F.bcol, F.val)
+               stream=None, allocator: sp2_allocator | None = None) -> c_void_p:
+    """F: a tile set (object with n, brow, bcol, val: numpy -> host copy, CUDA
+    tensors -> device copy), or a dense symmetric 2-D float64 numpy array / torch
+    tensor (sp2_create_dense).  ``allocator``: an sp2_allocator whose alloc/free
+    are ctypes callbacks (the caller keeps them alive), None = library pool."""
     ctx = c_void_p()
     prm = params if params is not None else sp2_default_params()
-    rc = load().sp2_create(byref(bsr), int(nocc), float(homo_ub), float(lumo_lb), float(tau), byref(prm), None,
-                           _stream_handle(stream), byref(ctx))
-    del keep
+    al = byref(allocator) if allocator is not None else None
+    if _is_dense(F):
+        if isinstance(F, np.ndarray):
+            Fd = np.ascontiguousarray(F, dtype=np.float64)
+        else:
+            import torch
+            Fd = F.to(torch.float64).contiguous()
+        ptr, on_dev = _ptr(Fd)
+        n = int(Fd.shape[0])
+        if Fd.shape[1] != n:
+            raise ValueError("dense F must be square")
+        rc = load().sp2_create_dense(c_void_p(ptr), n, n, on_dev, int(nocc), float(homo_ub), float(lumo_lb),
+                                     float(tau), byref(prm), al, _stream_handle(stream), byref(ctx))
+        del Fd
+    else:
+        bsr, keep = make_bsr(F.n, F.brow, F.bcol, F.val)
+        rc = load().sp2_create(byref(bsr), int(nocc), float(homo_ub), float(lumo_lb), float(tau), byref(prm), al,
+                               _stream_handle(stream), byref(ctx))
+        del keep
     if rc != SP2_OK:
         raise SP2Error(rc, "sp2_create")
     return ctx
@@ -231,6 +258,27 @@ def sp2_copy_D(ctx, out=None):
     if rc != SP2_OK:
         raise SP2Error(rc, "sp2_copy_D")
     return brow[: n.value], bcol[: n.value], val[: n.value]
+
+
+def sp2_copy_D_dense(ctx, out=None, device: bool = False):
+    """D as a dense symmetric matrix.  ``out``: a contiguous float64 n x n numpy
+    array / CPU tensor (host) or CUDA tensor (device); without it a new numpy
+    array (device=False) or CUDA tensor (device=True) is returned."""
+    v = sp2_get_D(ctx)
+    n = int(v.n)
+    if out is None:
+        if device:
+            import torch
+            out = torch.empty((n, n), dtype=torch.float64, device="cuda")
+        else:
+            out = np.empty((n, n), np.float64)
+    ptr, on_dev = _ptr(out)
+    if tuple(out.shape) != (n, n):
+        raise ValueError(f"out must be {n} x {n}")
+    rc = load().sp2_copy_D_dense(ctx, c_void_p(ptr), n, on_dev)
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_copy_D_dense")
+    return out
 
 
 def sp2_backward(ctx, W) -> sp2_bsr:
@@ -337,10 +385,11 @@ class SP2:
     """One SP2 context: create on construction, ``run()``, ``D_host()``,
     ``D_device()``, ``backward(W)``, ``close()``."""
 
-    def __init__(self, F, nocc, homo_ub, lumo_lb, tau, stream=None, **params):
+    def __init__(self, F, nocc, homo_ub, lumo_lb, tau, stream=None, allocator=None, **params):
         self.prm = sp2_default_params(**params)
         self.F = F
-        self.ctx = sp2_create(F, nocc, homo_ub, lumo_lb, tau, self.prm, stream)
+        self.allocator = allocator      # kept alive with the context
+        self.ctx = sp2_create(F, nocc, homo_ub, lumo_lb, tau, self.prm, stream, allocator)
         self.code = None
         self.stats = None
 
@@ -355,6 +404,9 @@ class SP2:
     def D_device(self):
         return device_view_to_torch(sp2_get_D(self.ctx))
 
+    def D_dense(self, out=None, device: bool = False):
+        return sp2_copy_D_dense(self.ctx, out, device)
+
     def backward(self, W):
         return device_view_to_torch(sp2_backward(self.ctx, W))
 
@@ -368,6 +420,26 @@ class SP2:
             self.close()
         except Exception:
             pass
+
+
+def run(F, nocc, homo_ub, lumo_lb, tau, stream=None, **params):
+    """One SP2 expansion: D and the run statistics.
+
+    F is a tile set (n, brow, bcol, val) or a dense symmetric matrix (numpy
+    array or torch tensor).  Returns (D, stats): for a dense F, D is dense
+    (numpy on the host, a CUDA tensor when F is a CUDA tensor); for a tile set,
+    D is (brow, bcol, val) on the host.  Raises SP2Error on failure; a run that
+    hits n_max without the stop test firing returns with stats["converged"] = 0."""
+    ctx = SP2(F, nocc, homo_ub, lumo_lb, tau, stream=stream, **params)
+    try:
+        st = ctx.run()
+        if _is_dense(F):
+            D = ctx.D_dense(device=not isinstance(F, np.ndarray) and bool(getattr(F, "is_cuda", False)))
+        else:
+            D = ctx.D_host()
+    finally:
+        ctx.close()
+    return D, st
 
 
 def header_functions() -> list[str]:
@@ -391,6 +463,8 @@ def _autograd_function():
 
         forward(F_val, F_brow, F_bcol, n, nocc, homo_ub, lumo_lb, tau, params)
         returns (D_val, D_brow, D_bcol); only D_val carries a gradient.
+        params: sp2_params fields by name, plus allow_not_converged (default
+        False: a run that reaches n_max without the stop test raises SP2Error).
         backward: for L with dL/dD_val = gD, W = gD on D's pattern with
         off-diagonal tiles halved (each stands for two blocks of the symmetric
         D), so L = trace(D W); sp2_backward gives dF_ij = dL/dF_ij, and a stored
@@ -400,9 +474,14 @@ def _autograd_function():
         def forward(ctx, F_val, F_brow, F_bcol, n, nocc, homo_ub, lumo_lb, tau, params=None):
             F = _Tiles(int(n), F_brow, F_bcol, F_val.detach())
             prm = dict(params or {})
+            allow = bool(prm.pop("allow_not_converged", False))
             prm["record_masks"] = 1
             obj = SP2(F, nocc, homo_ub, lumo_lb, tau, **prm)
             obj.run()
+            if obj.code == NOT_CONVERGED and not allow:
+                obj.close()
+                raise SP2Error(obj.code, "sp2_run (pass allow_not_converged=True in params to accept the last "
+                                         "iterate)")
             if obj.code not in (SP2_OK, NOT_CONVERGED):
                 raise SP2Error(obj.code, "sp2_run")
             d_brow, d_bcol, d_val = obj.D_device()
@@ -420,10 +499,11 @@ def _autograd_function():
             off = d_brow != d_bcol
             w[off] *= 0.5
             W = _Tiles(ctx.n, d_brow, d_bcol, w.contiguous())
+            # the context stays open until this autograd node is freed, so a
+            # second backward (retain_graph=True) runs the same recorded sweep
             _, _, dF = ctx.obj.backward(W)
             dF = dF.clone()
             dF[ctx.f_off] *= 2.0
-            ctx.obj.close()
             return dF, None, None, None, None, None, None, None, None
 
     return SP2Function

@@ -25,7 +25,9 @@ std::mutex g_mu;
 void* g_scratch_ptr[MAX_DEVICES] = {};
 
 // Device address of the scratch array on the current device, looked up once
-// per device (the host-side name of the array is not a device address).
+// per device (the host-side name of the array is not a device address).  The
+// address stays valid for the life of the device's primary context; a
+// cudaDeviceReset of that device invalidates it (see include/sp2.h).
 int scratch_for_current_device(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= MAX_DEVICES) {
@@ -67,13 +69,10 @@ extern "C" int sp2_truncate_noalloc(const int32_t* brow, const int32_t* bcol, co
   const int64_t nseg = mode == SP2_TRUNC_FROBINF ? nsb * nsb : 1;
   if (nnzb > NOALLOC_MAX_TILES || nseg > NOALLOC_MAX_SEGMENTS) return SP2_ERR_TOO_LARGE;
   if (nnzb == 0) return SP2_OK;
-  // scratch layout: tile norms, then the radix-select work area (budget units,
-  // segment ids, per-segment state, histograms, super-block flags and counts)
+  // scratch layout: tile norms, then the radix-select work area, sized by the
+  // same function that sizes it for sp2_truncate
   const size_t n2_bytes = align256((size_t)nnzb * 8);
-  const size_t need = n2_bytes + align256((size_t)nnzb * 8) + align256((size_t)nnzb * 4) +
-                      3 * align256((size_t)nseg * 8) + 3 * align256((size_t)nseg * 4) +
-                      align256((size_t)nseg * 256 * 8) + align256((size_t)(nsb * nsb) * 4) +
-                      align256((size_t)nsb * 4);
+  const size_t need = n2_bytes + trunc_work_bytes(nnzb, (int)nb64, part_tiles);
   if (need > NOALLOC_SCRATCH_BYTES) return SP2_ERR_TOO_LARGE;
   void* base = nullptr;
   const int rc = scratch_for_current_device(&base);

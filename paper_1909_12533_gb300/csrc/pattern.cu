@@ -168,14 +168,17 @@ __global__ void k_fill_full(const uint32_t* __restrict__ bits, int nb, int words
   }
 }
 
-// Row I of the product pattern: OR over K in A's row I of B's bitmap row K,
-// restricted to J >= I, plus the diagonal tile.
+// Row I of the pattern of X_i = c0 I + c1 X~ + c2 X~^2 (Algorithm 2): OR over K
+// in A's row I of B's bitmap row K (the product), OR A's own row I (the c1 X~
+// term: a stored tile whose diagonal tiles were truncated away and that no K
+// connects is still an output tile), restricted to J >= I, plus the diagonal.
 __global__ void k_product_bits(const int32_t* __restrict__ arowptr, const int32_t* __restrict__ acol,
-                               const uint32_t* __restrict__ bbits, int nb, int words, uint32_t* out) {
+                               const uint32_t* __restrict__ abits, const uint32_t* __restrict__ bbits, int nb,
+                               int words, uint32_t* out) {
   const int I = blockIdx.x;
   const int a0 = arowptr[I], a1 = arowptr[I + 1];
   for (int w = threadIdx.x; w < words; w += blockDim.x) {
-    uint32_t acc = 0;
+    uint32_t acc = abits[(int64_t)I * words + w];
     for (int e = a0; e < a1; ++e) acc |= bbits[(int64_t)acol[e] * words + w];
     const int lo = w * 32;
     if (lo + 32 <= I) acc = 0;
@@ -286,7 +289,7 @@ cudaError_t launch_fill_full(const TileSet& s, int nb, FullPattern& fp, cudaStre
 cudaError_t launch_product_bits(const FullPattern& a, const FullPattern& b, int nb, uint32_t* out_bits,
                                 cudaStream_t st) {
   const int t = a.words >= 128 ? 256 : (a.words >= 32 ? 128 : 32);
-  { ++g_launches; k_product_bits<<<nb, t, 0, st>>>(a.rowptr, a.col, b.bits, nb, a.words, out_bits); }
+  { ++g_launches; k_product_bits<<<nb, t, 0, st>>>(a.rowptr, a.col, a.bits, b.bits, nb, a.words, out_bits); }
   return cudaGetLastError();
 }
 

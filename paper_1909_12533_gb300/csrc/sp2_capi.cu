@@ -325,6 +325,7 @@ struct sp2_ctx {
   Buf y_brow, y_bcol, y_slot, y_rowptr;      // index set 1 (the next X~ while the stop test is pending)
   int xset = 0;
   int tail_from = 0;   // first iteration of the FP64 tail (0: none yet)
+  int selftest_pending = 0;   // error-path self-test still to run (1 timeout, 2 range)
   Buf o_brow, o_bcol, o_slot, o_rowptr, o_bits;
   Buf pool[2];
   int cur = 0;
@@ -578,8 +579,9 @@ TcOp prepare_operand(sp2_ctx* c, const TileSet& x, const double* pool, const Ful
                             c->st),
           "record index");
     c->ck(launch_panel_slices(ob.index.as<uint32_t>(), nrec, x.slot, pool, ob.data.p, ob.head.as<uint8_t>(), k,
-                              c->errflag.as<int32_t>(), scale, c->st),
+                              c->errflag.as<int32_t>(), scale, c->selftest_pending == 2, c->st),
           "record slices");
+    if (c->selftest_pending == 2) c->selftest_pending = 0;
   }
   TcOp op;
   op.sbits = ob.sbits.as<uint32_t>();
@@ -640,6 +642,9 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   c->ensure(c->tcscratch, (size_t)nsuper * 2 * 128 * 128 * 8);
   L.scratch = c->tcscratch.p;
   L.seg_min = c->prm.acc_flush_min;
+  L.wait_ns = (unsigned long long)c->prm.wait_limit_ms * 1000000ull;
+  L.selftest = c->selftest_pending == 1;
+  if (c->selftest_pending == 1) c->selftest_pending = 0;
   L.err = c->errflag.as<int32_t>();
   c->ck(cudaEventRecord(c->evs0, c->st), "event");
   c->ck(launch_square_tc(L, c->st), "square tc");
@@ -705,6 +710,8 @@ int sp2_default_params(sp2_params* p) {
   p->record_masks = 0;
   p->fp64_tail = 1e-4;
   p->acc_flush_min = 512;
+  p->wait_limit_ms = 2000;
+  p->selftest = 0;
   return SP2_OK;
 }
 
@@ -750,20 +757,23 @@ const char* sp2_strerror(int code) {
     case SP2_ERR_STATE: return "call out of order";
     case SP2_ERR_CAPACITY: return "buffer too small";
     case SP2_ERR_TOO_LARGE: return "input exceeds the fixed scratch of the allocation-free entry point";
+    case SP2_ERR_RANGE: return "an iterate left the range of the method (bounds do not bracket the gap, or divergence)";
     default: return "unknown error";
   }
 }
 
-int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, double tau,
-               const sp2_params* params, const sp2_allocator* alloc, void* cuda_stream, sp2_ctx** out) {
-  if (!out) return SP2_ERR_INVALID_ARG;
-  *out = nullptr;
-  if (!F || F->b != TB || F->n <= 0 || F->nnzb <= 0 || !F->brow || !F->bcol || !F->val) return SP2_ERR_INVALID_ARG;
+}  // extern "C"
+
+namespace {
+
+// Argument checks shared by sp2_create and sp2_create_dense; fills prm.
+int check_create_args(int64_t n, double homo_ub, double lumo_lb, double tau, const sp2_params* params,
+                      const sp2_allocator* alloc, sp2_params& prm) {
+  if (n <= 0) return SP2_ERR_INVALID_ARG;
   if (!std::isfinite(homo_ub) || !std::isfinite(lumo_lb) || !std::isfinite(tau) || tau < 0.0)
     return SP2_ERR_INVALID_ARG;
   if (!(homo_ub < lumo_lb)) return SP2_ERR_BOUNDS;
   if (alloc && (!alloc->alloc || !alloc->free)) return SP2_ERR_INVALID_ARG;
-  sp2_params prm;
   sp2_default_params(&prm);
   if (params) prm = *params;
   if (prm.mode != SP2_MODE_SP2 && prm.mode != SP2_MODE_SP2ACC) return SP2_ERR_INVALID_ARG;
@@ -776,11 +786,16 @@ int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, d
   if (prm.precision != SP2_PREC_FP64 && prm.precision != SP2_PREC_SPLIT16) return SP2_ERR_INVALID_ARG;
   if (prm.precision == SP2_PREC_SPLIT16 && (prm.slices < 2 || prm.slices > 4)) return SP2_ERR_INVALID_ARG;
   if (prm.ckpt_every < 1) return SP2_ERR_INVALID_ARG;
-  const int64_t nb64 = (F->n + TB - 1) / TB;
+  if (prm.wait_limit_ms < 1 || prm.selftest < 0 || prm.selftest > 2) return SP2_ERR_INVALID_ARG;
+  const int64_t nb64 = (n + TB - 1) / TB;
   if (nb64 > 65535) return SP2_ERR_INVALID_ARG;
+  return SP2_OK;
+}
 
+sp2_ctx* new_ctx(const sp2_params& prm, const sp2_allocator* alloc, void* cuda_stream, int64_t n, int64_t nocc,
+                 double homo_ub, double lumo_lb, double tau) {
   sp2_ctx* c = new (std::nothrow) sp2_ctx();
-  if (!c) return SP2_ERR_OOM;
+  if (!c) return nullptr;
   c->st = static_cast<cudaStream_t>(cuda_stream);
   c->al.st = c->st;
   if (alloc) {
@@ -790,69 +805,165 @@ int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, d
     c->al.pool = device_pool();
   }
   c->prm = prm;
-  c->n = F->n;
-  c->nb = (int)nb64;
+  c->selftest_pending = prm.selftest;
+  c->n = n;
+  c->nb = (int)((n + TB - 1) / TB);
   c->words = (c->nb + 31) / 32;
   c->nocc = nocc;
   c->homo_ub = homo_ub;
   c->lumo_lb = lumo_lb;
   c->tau = tau;
+  return c;
+}
+
+void init_ctx_resources(sp2_ctx* c) {
+  c->ck(cudaEventCreate(&c->ev0), "event");
+  c->ck(cudaEventCreate(&c->ev1), "event");
+  c->ck(cudaEventCreate(&c->evs0), "event");
+  c->ck(cudaEventCreate(&c->evs1), "event");
+  c->hb = take_host_block();
+  if (!c->hb) {
+    c->last_error = "page-locked host allocation failed";
+    throw Fail{SP2_ERR_OOM};
+  }
+  c->h_sc = &c->hb->sc;
+  c->h_cnt = c->hb->cnt;
+  c->h_d2 = c->hb->d2;
+}
+
+// F's nnzb tiles are in f_brow / f_bcol / f_pool: validate them, then Step 1
+// of Section 4 (Gershgorin bounds, schedule).
+void finish_create(sp2_ctx* c, int64_t nnzb) {
+  c->ensure(c->dcnt, 16);
+  c->ck(launch_check_pattern(c->f_brow.as<int32_t>(), c->f_bcol.as<int32_t>(), nnzb, c->nb, c->f_pool.as<double>(),
+                             c->n, c->dcnt.as<int32_t>(), c->st),
+        "check");
+  c->ck(cudaMemcpyAsync(c->h_cnt, c->dcnt.p, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
+  c->sync();
+  if (c->h_cnt[0] & 1) throw Fail{SP2_ERR_PATTERN};
+  if (c->h_cnt[1] != c->nb) throw Fail{SP2_ERR_PATTERN};
+  if (c->h_cnt[0] & 2) throw Fail{SP2_ERR_NONFINITE};
+  // slots of F are the identity
+  c->ensure(c->f_slot, nnzb * 4);
+  c->ensure(c->f_rowptr, (c->nb + 1) * 4);
+  c->ck(launch_iota(c->f_slot.as<int32_t>(), nnzb, c->st), "slots");
+  set_tiles(c->F, c->f_brow, c->f_bcol, c->f_slot, c->f_rowptr, nnzb);
+  c->ck(launch_rowptr_from_brow(c->F.brow, nnzb, c->nb, c->F.rowptr, c->st), "rowptr");
+  // Gershgorin (Section 4, Step 1)
+  build_full(c, c->F, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
+  c->ensure(c->rowlo, c->n * 8);
+  c->ensure(c->rowhi, c->n * 8);
+  c->ensure(c->d2, 16);
+  c->ck(launch_gershgorin(c->fp, c->f_pool.as<double>(), c->nb, c->n, c->rowlo.as<double>(), c->rowhi.as<double>(),
+                          c->st),
+        "gershgorin");
+  c->ck(launch_minmax(c->rowlo.as<double>(), c->rowhi.as<double>(), c->n, c->d2.as<double>(), c->st), "minmax");
+  c->ck(cudaMemcpyAsync(c->h_d2, c->d2.p, 16, cudaMemcpyDeviceToHost, c->st), "d2h");
+  c->sync();
+  const double lmin = c->h_d2[0], lmax = c->h_d2[1];
+  if (!(lmin <= c->homo_ub) || !(c->lumo_lb <= lmax) || !(lmax > lmin)) throw Fail{SP2_ERR_BOUNDS};
+  const sp2_params& prm = c->prm;
+  c->sch = make_schedule(lmin, lmax, c->homo_ub, c->lumo_lb, c->tau, prm.gamma, prm.mode == SP2_MODE_SP2ACC,
+                         prm.delta_acc, prm.n_max_cap);
+  fill_stats_sched(c);
+  c->stats.status = SP2_OK;
+  c->stats.homo_est = c->stats.lumo_est = NAN;
+}
+
+int create_fail(sp2_ctx* c, const Fail& f) {
+  if (f.code == SP2_ERR_CUDA || f.code == SP2_ERR_OOM) fprintf(stderr, "sp2_create: %s\n", c->last_error.c_str());
+  sp2_destroy(c);
+  return f.code;
+}
+
+}  // namespace
+
+extern "C" {
+
+int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, double tau,
+               const sp2_params* params, const sp2_allocator* alloc, void* cuda_stream, sp2_ctx** out) {
+  if (!out) return SP2_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!F || F->b != TB || F->n <= 0 || F->nnzb <= 0 || !F->brow || !F->bcol || !F->val) return SP2_ERR_INVALID_ARG;
+  sp2_params prm;
+  const int rc = check_create_args(F->n, homo_ub, lumo_lb, tau, params, alloc, prm);
+  if (rc != SP2_OK) return rc;
+  sp2_ctx* c = new_ctx(prm, alloc, cuda_stream, F->n, nocc, homo_ub, lumo_lb, tau);
+  if (!c) return SP2_ERR_OOM;
   try {
-    c->ck(cudaEventCreate(&c->ev0), "event");
-    c->ck(cudaEventCreate(&c->ev1), "event");
-    c->ck(cudaEventCreate(&c->evs0), "event");
-    c->ck(cudaEventCreate(&c->evs1), "event");
-    c->hb = take_host_block();
-    if (!c->hb) throw Fail{SP2_ERR_OOM};
-    c->h_sc = &c->hb->sc;
-    c->h_cnt = c->hb->cnt;
-    c->h_d2 = c->hb->d2;
+    init_ctx_resources(c);
     const int64_t nnzb = F->nnzb;
     const cudaMemcpyKind kind = F->on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
     c->ensure(c->f_brow, nnzb * 4);
     c->ensure(c->f_bcol, nnzb * 4);
-    c->ensure(c->f_slot, nnzb * 4);
-    c->ensure(c->f_rowptr, (c->nb + 1) * 4);
     c->ensure(c->f_pool, (size_t)nnzb * TE * 8);
     c->ck(cudaMemcpyAsync(c->f_brow.p, F->brow, nnzb * 4, kind, c->st), "copy F");
     c->ck(cudaMemcpyAsync(c->f_bcol.p, F->bcol, nnzb * 4, kind, c->st), "copy F");
     c->ck(cudaMemcpyAsync(c->f_pool.p, F->val, (size_t)nnzb * TE * 8, kind, c->st), "copy F");
-    // validation: sorted upper pattern, every diagonal tile, finite values
-    c->ensure(c->dcnt, 16);
-    c->ck(launch_check_pattern(c->f_brow.as<int32_t>(), c->f_bcol.as<int32_t>(), nnzb, c->nb, c->f_pool.as<double>(),
-                               c->n, c->dcnt.as<int32_t>(), c->st),
-          "check");
-    c->ck(cudaMemcpyAsync(c->h_cnt, c->dcnt.p, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
-    c->sync();
-    if (c->h_cnt[0] & 1) throw Fail{SP2_ERR_PATTERN};
-    if (c->h_cnt[1] != c->nb) throw Fail{SP2_ERR_PATTERN};
-    if (c->h_cnt[0] & 2) throw Fail{SP2_ERR_NONFINITE};
-    // slots of F are the identity
-    c->ck(launch_iota(c->f_slot.as<int32_t>(), nnzb, c->st), "slots");
-    set_tiles(c->F, c->f_brow, c->f_bcol, c->f_slot, c->f_rowptr, nnzb);
-    c->ck(launch_rowptr_from_brow(c->F.brow, nnzb, c->nb, c->F.rowptr, c->st), "rowptr");
-    // Gershgorin (Section 4, Step 1)
-    build_full(c, c->F, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
-    c->ensure(c->rowlo, c->n * 8);
-    c->ensure(c->rowhi, c->n * 8);
-    c->ensure(c->d2, 16);
-    c->ck(launch_gershgorin(c->fp, c->f_pool.as<double>(), c->nb, c->n, c->rowlo.as<double>(), c->rowhi.as<double>(),
-                            c->st),
-          "gershgorin");
-    c->ck(launch_minmax(c->rowlo.as<double>(), c->rowhi.as<double>(), c->n, c->d2.as<double>(), c->st), "minmax");
-    c->ck(cudaMemcpyAsync(c->h_d2, c->d2.p, 16, cudaMemcpyDeviceToHost, c->st), "d2h");
-    c->sync();
-    const double lmin = c->h_d2[0], lmax = c->h_d2[1];
-    if (!(lmin <= homo_ub) || !(lumo_lb <= lmax) || !(lmax > lmin)) throw Fail{SP2_ERR_BOUNDS};
-    c->sch = make_schedule(lmin, lmax, homo_ub, lumo_lb, tau, prm.gamma, prm.mode == SP2_MODE_SP2ACC, prm.delta_acc,
-                           prm.n_max_cap);
-    fill_stats_sched(c);
-    c->stats.status = SP2_OK;
-    c->stats.homo_est = c->stats.lumo_est = NAN;
+    finish_create(c, nnzb);
   } catch (const Fail& f) {
-    if (f.code == SP2_ERR_CUDA || f.code == SP2_ERR_OOM) fprintf(stderr, "sp2_create: %s\n", c->last_error.c_str());
-    sp2_destroy(c);
-    return f.code;
+    return create_fail(c, f);
+  }
+  *out = c;
+  return SP2_OK;
+}
+
+int sp2_create_dense(const double* F, int64_t n, int64_t ld, int32_t on_device, int64_t nocc, double homo_ub,
+                     double lumo_lb, double tau, const sp2_params* params, const sp2_allocator* alloc,
+                     void* cuda_stream, sp2_ctx** out) {
+  if (!out) return SP2_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!F || n <= 0 || ld < n) return SP2_ERR_INVALID_ARG;
+  sp2_params prm;
+  const int rc = check_create_args(n, homo_ub, lumo_lb, tau, params, alloc, prm);
+  if (rc != SP2_OK) return rc;
+  const int64_t nb64 = (n + TB - 1) / TB;
+  if (nb64 * nb64 >= (int64_t)1 << 31) return SP2_ERR_INVALID_ARG;   // tile flags are indexed by int32
+  sp2_ctx* c = new_ctx(prm, alloc, cuda_stream, n, nocc, homo_ub, lumo_lb, tau);
+  if (!c) return SP2_ERR_OOM;
+  void* tmp = nullptr;
+  try {
+    init_ctx_resources(c);
+    const double* dF = F;
+    int64_t dld = ld;
+    if (!on_device) {
+      // device copy of the host matrix (leading dimension n)
+      tmp = c->al.get((size_t)n * n * 8);
+      if (!tmp) {
+        c->last_error = "device allocation of the dense F copy failed";
+        throw Fail{SP2_ERR_OOM};
+      }
+      c->ck(cudaMemcpy2DAsync(tmp, (size_t)n * 8, F, (size_t)ld * 8, (size_t)n * 8, (size_t)n,
+                              cudaMemcpyHostToDevice, c->st),
+            "copy F");
+      dF = static_cast<const double*>(tmp);
+      dld = n;
+    }
+    const int nb = c->nb;
+    const int64_t nflag = (int64_t)nb * nb;
+    c->ensure(c->scanbuf, (size_t)nflag * 4);   // tile flags
+    c->ensure(c->keep, (size_t)nflag * 4);      // their exclusive scan
+    c->ensure(c->dcnt, 16);
+    c->ensure(c->scantmp, scan_tmp_bytes(nflag) + 4096);
+    c->ck(launch_dense_tile_flags(dF, n, dld, nb, c->scanbuf.as<int32_t>(), c->st), "tile flags");
+    c->ck(launch_scan_i32(c->scanbuf.as<int32_t>(), c->keep.as<int32_t>(), nflag, c->dcnt.as<int32_t>(),
+                          c->scantmp.p, c->st),
+          "scan");
+    const int64_t nnzb = read_count(c, c->dcnt.as<int32_t>());
+    c->ensure(c->f_brow, nnzb * 4);
+    c->ensure(c->f_bcol, nnzb * 4);
+    c->ensure(c->f_pool, (size_t)nnzb * TE * 8);
+    c->ck(launch_dense_tile_fill(dF, n, dld, nb, c->scanbuf.as<int32_t>(), c->keep.as<int32_t>(),
+                                 c->f_brow.as<int32_t>(), c->f_bcol.as<int32_t>(), c->f_pool.as<double>(), c->st),
+          "tile fill");
+    if (tmp) {
+      c->al.put(tmp);
+      tmp = nullptr;
+    }
+    finish_create(c, nnzb);
+  } catch (const Fail& f) {
+    if (tmp) c->al.put(tmp);
+    return create_fail(c, f);
   }
   *out = c;
   return SP2_OK;
@@ -967,6 +1078,11 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
         fprintf(stderr, "sp2_run: %s\n", c->last_error.c_str());
         throw Fail{SP2_ERR_TIMEOUT};
       }
+      if (c->h_cnt[2] & 4) {
+        c->last_error = "an element of the iterate reached |x| >= 2, outside the range of the tensor-core slices";
+        fprintf(stderr, "sp2_run: %s\n", c->last_error.c_str());
+        throw Fail{SP2_ERR_RANGE};
+      }
       if (tc) {
         // slice-pair products issued, each two 128 x 128 x 16 MMAs
         const long long products = *reinterpret_cast<long long*>(c->h_d2);
@@ -980,6 +1096,11 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       const int j = i - 1;
       const double ej = std::sqrt(std::max(c->h_sc->e2, 0.0));
       const double tj = c->h_sc->trX - c->h_sc->trS;
+      if (!std::isfinite(ej) || !std::isfinite(tj)) {
+        c->last_error = "e_j or t_j is not finite";
+        fprintf(stderr, "sp2_run: %s\n", c->last_error.c_str());
+        throw Fail{SP2_ERR_RANGE};
+      }
       ev.push_back(ej);
       tv.push_back(tj);
       S.e[j] = ej;
@@ -1064,6 +1185,39 @@ int sp2_copy_D(sp2_ctx* c, int32_t* brow, int32_t* bcol, double* val, int64_t ca
     c->ck(cudaMemcpyAsync(val, c->d_val.p, (size_t)c->d_nnzb * TE * 8, k, c->st), "copy D");
     c->sync();
   } catch (const Fail& f) {
+    return f.code;
+  }
+  return SP2_OK;
+}
+
+int sp2_copy_D_dense(sp2_ctx* c, double* out, int64_t ld, int32_t on_device) {
+  if (!c || !out || ld < c->n) return SP2_ERR_INVALID_ARG;
+  if (!c->have_D) return SP2_ERR_STATE;
+  void* tmp = nullptr;
+  try {
+    double* dst = out;
+    int64_t dld = ld;
+    if (!on_device) {
+      tmp = c->al.get((size_t)c->n * c->n * 8);
+      if (!tmp) {
+        c->last_error = "device allocation of the dense D buffer failed";
+        throw Fail{SP2_ERR_OOM};
+      }
+      dst = static_cast<double*>(tmp);
+      dld = c->n;
+    }
+    c->ck(launch_tiles_to_dense(c->d_brow.as<int32_t>(), c->d_bcol.as<int32_t>(), c->d_val.as<double>(), c->d_nnzb,
+                                c->n, dld, dst, c->st),
+          "dense D");
+    if (!on_device)
+      c->ck(cudaMemcpy2DAsync(out, (size_t)ld * 8, dst, (size_t)c->n * 8, (size_t)c->n * 8, (size_t)c->n,
+                              cudaMemcpyDeviceToHost, c->st),
+            "copy D");
+    c->sync();
+    if (tmp) c->al.put(tmp);
+  } catch (const Fail& f) {
+    if (tmp) c->al.put(tmp);
+    if (f.code == SP2_ERR_CUDA || f.code == SP2_ERR_OOM) fprintf(stderr, "sp2_copy_D_dense: %s\n", c->last_error.c_str());
     return f.code;
   }
   return SP2_OK;
@@ -1220,6 +1374,10 @@ int sp2_backward(sp2_ctx* c, const sp2_bsr* W, sp2_bsr* dF) {
     if (c->h_cnt[2] & 1) {
       c->last_error = "tensor-core adjoint: a bounded wait timed out";
       throw Fail{SP2_ERR_TIMEOUT};
+    }
+    if (c->h_cnt[2] & 4) {
+      c->last_error = "an element of an adjoint operand reached the edge of the tensor-core slices";
+      throw Fail{SP2_ERR_RANGE};
     }
     float ms = 0.f;
     c->ck(cudaEventElapsedTime(&ms, c->ev0, c->ev1), "elapsed");

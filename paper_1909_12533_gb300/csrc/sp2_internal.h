@@ -114,6 +114,15 @@ cudaError_t launch_place(const TileSet& src, const double* spool, const TileSet&
                          int sym_diag, cudaStream_t st);
 cudaError_t launch_iota(int32_t* p, int64_t n, cudaStream_t st);
 
+// dense.cu: dense row-major matrix <-> upper tiles
+// flag[I * nb + J] = 1 for every diagonal tile and every nonzero tile with J > I
+cudaError_t launch_dense_tile_flags(const double* F, int64_t n, int64_t ld, int nb, int32_t* flag, cudaStream_t st);
+cudaError_t launch_dense_tile_fill(const double* F, int64_t n, int64_t ld, int nb, const int32_t* flag,
+                                   const int32_t* pos, int32_t* brow, int32_t* bcol, double* pool, cudaStream_t st);
+// out := the symmetric matrix of the upper tiles (zero elsewhere), leading dimension ld
+cudaError_t launch_tiles_to_dense(const int32_t* brow, const int32_t* bcol, const double* val, int64_t nnzb,
+                                  int64_t n, int64_t ld, double* out, cudaStream_t st);
+
 // square_tc.cu: tcgen05 FP16-slice product (see the file header).  An
 // operand is stored as panel records: for each super-row R (tile rows
 // 4R..4R+3) and K tile present in its super-row bitmap, a header byte and the
@@ -146,10 +155,15 @@ struct TcLaunch {
   int32_t* err;
   void* scratch;             // nsuper * 2 * 128 * 128 int64 (epilogue staging, two tiles per CTA)
   int seg_min;               // K loops of at least this many steps are accumulated in 16-step segments (0: never)
+  unsigned long long wait_ns = 2000000000ull;   // limit of every bounded wait in the kernel
+  bool selftest = false;     // wait first on a barrier nothing arrives at (tests the timeout path)
 };
 size_t panel_record_bytes(int k);
+// report_range: also report an out-of-range element (error bit 4) without one
+// being present (self-test of the error path)
 cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32_t* slot, const double* pool,
-                                void* data, uint8_t* head, int k, int32_t* err, double scale, cudaStream_t st);
+                                void* data, uint8_t* head, int k, int32_t* err, double scale, bool report_range,
+                                cudaStream_t st);
 cudaError_t launch_popc_words(const uint32_t* bits, int64_t n, int32_t* cnt, cudaStream_t st);
 cudaError_t launch_panel_fill(const FullPattern& fp, int nb, const uint32_t* sbits, const int32_t* spos,
                               uint32_t* index, cudaStream_t st);

@@ -52,7 +52,6 @@ namespace {
 
 constexpr int ST = 128;          // super-tile edge (4 tiles)
 constexpr int SLICE_BYTES = 2048;  // one 32 x 32 FP16 slice
-constexpr unsigned long long WAIT_NS = 2000000000ull;   // bounded waits give up after ~2 s
 
 // ------------------------------------------------------------------ PTX helpers
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -105,28 +104,34 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
   return ok != 0;
 }
 
-// Timeout sites of a launch, for the error message (err[1], bit 1 producer
-// stage, 2 producer tile slot, 3 MMA data, 4 MMA TMEM or segment slot, 5 MMA
+// Timeout sites of a launch, for the error message (err[1], bit 0 self-test
+// probe, 1 producer stage, 2 producer tile slot, 3 MMA data, 4 MMA TMEM or segment slot, 5 MMA
 // drain, 6 epilogue tile, 7 epilogue segment).
 __device__ __forceinline__ void note_timeout(int32_t* err, int where) {
   if (err) atomicOr(err + 1, 1 << where);
 }
 
+// Limit of every bounded wait of a launch (ns), set from the launch arguments.
+__device__ __forceinline__ unsigned long long& wait_limit_ns() {
+  __shared__ unsigned long long lim;
+  return lim;
+}
+
 // Bounded wait with suspension between polls: false on timeout.
 __device__ __forceinline__ bool mbar_wait_sleep(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = now_ns();
+  const unsigned long long t0 = now_ns(), lim = wait_limit_ns();
   while (!mbar_try_wait_sleep(bar, parity, 20000u))
-    if (now_ns() - t0 > WAIT_NS) return false;
+    if (now_ns() - t0 > lim) return false;
   return true;
 }
 
 // Bounded wait: false on timeout.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = now_ns();
+  const unsigned long long t0 = now_ns(), lim = wait_limit_ns();
   while (!mbar_try_wait(bar, parity))
-    if (now_ns() - t0 > WAIT_NS) return false;
+    if (now_ns() - t0 > lim) return false;
   return true;
 }
 
@@ -147,15 +152,6 @@ __device__ __forceinline__ long long f32_int_to_ll(float x) {
   const int ih = __float_as_int(hi + 12582912.0f) - 0x4B400000;
   const int il = __float_as_int(lo + 12582912.0f) - 0x4B400000;
   return (long long)ih * 2048 + il;
-}
-
-// Float of a double from its high word (sign, exponent, 20 mantissa bits):
-// relative error below 2^-20, |x| < 2^-126 gives 0.  Integer pipes only.
-__device__ __forceinline__ float f64_hi_to_f32(double x) {
-  const uint32_t hi = (uint32_t)__double2hiint(x);
-  const uint32_t e = (hi >> 20) & 0x7FFu;
-  const uint32_t f = (hi & 0x80000000u) | ((e - 896u) << 23) | ((hi & 0xFFFFFu) << 3);
-  return __uint_as_float(e > 896u ? f : 0u);
 }
 
 // x * 2^k, exact, by exponent arithmetic on the high word; x an integer-valued
@@ -228,11 +224,12 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 template <int K>
 __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ index, const int32_t* __restrict__ slot,
                                                        const double* __restrict__ pool, __half* data,
-                                                       uint8_t* head, int32_t* err, int lscale) {
+                                                       uint8_t* head, int32_t* err, int lscale, int report_range) {
   __shared__ __align__(16) __half sm[K * 4 * TE];
   __shared__ uint32_t wnz[8];
   __shared__ int first_s;
   const int64_t e = blockIdx.x;
+  if (report_range && e == 0 && threadIdx.x == 0 && err) atomicOr(err, 4);
   const uint4 iw = index[e];
   const uint32_t wd[4] = {iw.x, iw.y, iw.z, iw.w};
   constexpr int FIN = 11 * K - 1;                  // finest grid 2^-FIN
@@ -404,6 +401,8 @@ struct TcArgs {
   int32_t* err;
   long long* scratch;       // per CTA, 2 slots: 128 x 128 fixed-point sums of a tile in its epilogue
   int seg_min;              // K loops of at least this many steps are cut into 16-step segments (0: never)
+  unsigned long long wait_ns;   // limit of every bounded wait
+  int selftest;             // 1: the producer first waits on a barrier nothing arrives at (timeout path test)
 };
 
 // A pipeline stage holds one sub-step: two A units and two B units, a unit
@@ -452,7 +451,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   uint64_t* tile_empty = tile_full + 2;    // [2] epilogue done with the tile slot (one arrive per warp)
   uint64_t* drain = tile_empty + 2;        // MMAs issued before the exit are complete
   uint64_t* tmem_empty = drain + 1;        // [SEG_RING] every epilogue warp has read the segment's TMEM
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tmem_empty + SEG_RING);
+  uint64_t* probe = tmem_empty + SEG_RING; // self-test: a barrier that nothing arrives at
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(probe + 1);
   int32_t* tslot = reinterpret_cast<int32_t*>(tmem_slot + 2);      // [2] super-tile list index, -1: none
   int32_t* kcount = tslot + 2;                                      // [2][16] triplets per output tile
   uint32_t* gmap = reinterpret_cast<uint32_t*>(kcount + 32);       // [SEG_RING] groups written, block of each, last flag
@@ -475,8 +475,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       mbar_init(&tile_empty[b], EPI_WARPS);
     }
     mbar_init(drain, 1);
+    mbar_init(probe, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     status[0] = 0;
+    wait_limit_ns() = a.wait_ns;
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(smem_u32(tmem_slot))
@@ -541,6 +543,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       else ++step;
       return __shfl_sync(FULLW, r ? 1 : 0, 0) != 0;
     };
+    // self-test of the timeout path: before any copy is issued, wait on a
+    // barrier that nothing arrives at; the wait gives up after the wait limit,
+    // the status is set, and the launch ends through the no-more-tiles path
+    if (a.selftest) {
+      int good = 1;
+      if (lane == 0) good = mbar_wait(probe, 0) ? 1 : 0;
+      good = __shfl_sync(FULLW, good, 0);
+      if (!good && lane == 0) {
+        status[0] = 1;
+        note_timeout(a.err, 0);
+      }
+      __syncwarp();
+    }
     for (int it = 0; ok; ++it) {
       const int b = it & 1;
       // the slot's previous tile (it - 2) has left the epilogue
@@ -939,10 +954,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           const int64_t zi = (int64_t)(a.zref[zp] & ~REF_T);
           Zt = a.zpool + (int64_t)(a.zslot ? a.zslot[zi] : zi) * TE;
         }
-        double trS = 0.0, trX = 0.0, n2 = 0.0;
-        // ||X~ - S||^2 only steers the stopping test: FP64 differences, squared
-        // and summed in FP32
-        float e2f = 0.0f;
+        double trS = 0.0, trX = 0.0, n2 = 0.0, e2 = 0.0;
         double* O = a.opool + (int64_t)oi * TE;
         for (int ch = 0; ch < 2; ++ch) {     // 16 columns per chunk
           const int col0 = bt * 32 + ch * 16;
@@ -982,8 +994,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             else if (form == 2) xn = twice(z) - S;
             else xn = fma(a.c2, S, fma(a.c1, z, dg ? a.c0 : 0.0));
             out[i] = xn;
-            const float df = f64_hi_to_f32(z - S);
-            e2f = fmaf(df, df, e2f);
+            const double df = z - S;
+            e2 = fma(df, df, e2);
             n2 = fma(xn, xn, n2);
             if (dg) { trS += S; trX += z; }
           }
@@ -992,7 +1004,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           for (int i = 0; i < 8; ++i) op[i] = make_double2(out[2 * i], out[2 * i + 1]);
         }
         // warp reductions (the tile's 32 rows are this warp's 32 lanes)
-        double e2 = (double)e2f;
         for (int o = 16; o > 0; o >>= 1) {
           e2 += __shfl_xor_sync(FULLW, e2, o);
           n2 += __shfl_xor_sync(FULLW, n2, o);
@@ -1027,16 +1038,18 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 size_t panel_record_bytes(int k) { return (size_t)k * UNIT_BYTES; }
 
 cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32_t* slot, const double* pool,
-                                void* data, uint8_t* head, int k, int32_t* err, double scale, cudaStream_t st) {
+                                void* data, uint8_t* head, int k, int32_t* err, double scale, bool report_range,
+                                cudaStream_t st) {
   if (nrec == 0) return cudaSuccess;
   const uint4* ix = reinterpret_cast<const uint4*>(index);
   __half* d = static_cast<__half*>(data);
   const int ls = ilogb(scale);   // scale is a power of two
+  const int rr = report_range ? 1 : 0;
   const unsigned g = (unsigned)nrec;
   ++g_launches;
-  if (k == 2) k_panel_slices<2><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls);
-  else if (k == 3) k_panel_slices<3><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls);
-  else k_panel_slices<4><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls);
+  if (k == 2) k_panel_slices<2><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
+  else if (k == 3) k_panel_slices<3><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
+  else k_panel_slices<4><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
   return cudaGetLastError();
 }
 
@@ -1151,6 +1164,8 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   a.part = L.part; a.c0 = L.c0; a.c1 = L.c1; a.c2 = L.c2; a.scale = L.scale; a.n = L.n; a.nb = L.nb;
   a.words = L.words; a.nsr = L.nsr; a.err = L.err; a.scratch = static_cast<long long*>(L.scratch);
   a.seg_min = L.seg_min;
+  a.wait_ns = L.wait_ns;
+  a.selftest = L.selftest ? 1 : 0;
   cudaError_t e = cudaSuccess;
   switch (L.k) {
     case 2:

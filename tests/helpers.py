@@ -45,6 +45,9 @@ def compare(g, o, d_tol=1e-10):
     assert st["p"][1:] == sch.p[1:]
     np.testing.assert_allclose(st["alpha"][1:], sch.alpha[1:], rtol=1e-14)
     assert st["n"] == o.n, (st["n"], o.n)
+    # the numerator of every FLOP/s figure: (I <= J, K) tile triplets over all squares
+    assert st["tile_triplets"] == o.tile_triplets, (st["tile_triplets"], o.tile_triplets)
+    assert st["squares"] == o.squares
     assert bool(st["converged"]) == o.converged
     ne = len(o.e)
     assert len(st["e"]) == ne

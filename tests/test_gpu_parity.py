@@ -179,3 +179,34 @@ def test_contexts_reuse_pooled_memory_and_release():
     brow, bcol, val = ctx.D_host(buf)
     ctx.close()
     assert np.array_equal(brow, g["brow"]) and np.array_equal(val, g["val"])
+
+
+# ----------------------------------------------------------------- Step 3 estimates
+@pytest.mark.parametrize("key", [1, "2s", "4s"])
+def test_homo_lumo_estimates_match_oracle(key):
+    # Section 4 Step 3: the estimates come from e_j and t_j, which the GPU path
+    # computes to ~1e-10 relative; the same reading of Step 3 then gives the
+    # same estimates
+    c = _case(key)
+    kw = dict(stop=c["stop"])
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    st = g["stats"]
+    oh, ol = o.estimates
+    assert st["have_estimates"] == (1 if oh is not None else 0) | (2 if ol is not None else 0)
+    if oh is not None:
+        assert abs(st["homo_est"] - oh) <= 1e-8 * max(1.0, abs(oh))
+    if ol is not None:
+        assert abs(st["lumo_est"] - ol) <= 1e-8 * max(1.0, abs(ol))
+
+
+def test_homo_lumo_estimates_near_exact_eigenvalues_plain_sp2():
+    # plain SP2 (the paper's first run is unaccelerated, Section 6) on the dense
+    # 512 case: the estimates are within 0.02 of the exact homo and lumo
+    c = _case(1)
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], 0.0, stop="idempotency", mode="sp2")
+    st = g["stats"]
+    ev = c["eigenvalues"]
+    assert st["have_estimates"] == 3
+    assert abs(st["homo_est"] - ev[c["nocc"] - 1]) < 0.02
+    assert abs(st["lumo_est"] - ev[c["nocc"]]) < 0.02

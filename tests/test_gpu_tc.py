@@ -33,16 +33,46 @@ def test_split16_k4_meets_tolerance(key):
 
 def test_split16_first_square_matches_fp64_closely():
     # one step only: e_0, t_0 come from S = X~_0^2; slices on a 2^-43 grid.  The
-    # tensor path sums ||X~ - S||^2 (which only steers the stopping test) in FP32
-    # from FP64 differences; t uses FP64 traces.
+    # tensor path sums ||X~ - S||^2 in FP64 like the FP64 path, so e and t differ
+    # only by the products' rounding: |e_a - e_b| <= ||S_a - S_b||_F, each
+    # element within ~2^-44 (5.9M elements: < 1e-9 in norm)
     c = make_config("2s")
     a = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], n_max_cap=1)
     b = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], n_max_cap=1, precision="split16", slices=4)
     ea, eb = a["stats"]["e"], b["stats"]["e"]
-    np.testing.assert_allclose(eb, ea, rtol=1e-5)
-    np.testing.assert_allclose(b["stats"]["t"], a["stats"]["t"], rtol=1e-9)
+    np.testing.assert_allclose(eb, ea, rtol=1e-12, atol=1e-9)
+    np.testing.assert_allclose(b["stats"]["t"], a["stats"]["t"], rtol=1e-12, atol=1e-9)
     # 5.9M elements, each within ~1e-12 (2^-44 grid, FP32-exact groups)
     assert np.linalg.norm(a["D"] - b["D"]) < 1e-8
+
+
+def test_split16_precision_form_config3_analogue():
+    # the precision form of the water-like recipe (203 molecules, tau = 1e-5):
+    # the tensor path against the oracle at the mixed-path tolerance
+    c = make_config("3s")
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"])
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], precision="split16", slices=4)
+    err = _err(g, o)
+    print(f"3s split16: ||D-Dref||_F = {err:.3e}, n = {g['stats']['n']} (oracle {o.n})")
+    assert g["code"] == 0 and err <= MIXED_TOL
+    assert abs(g["stats"]["n"] - o.n) <= 1
+
+
+@pytest.mark.parametrize("mixed_from", [1, 8])
+def test_split16_narrow_gap_dense_segmented_accumulation(mixed_from):
+    # dense N = 1000 with gap 0.05 (the narrow-gap recipe at oracle size);
+    # acc_flush_min = 1 cuts every K loop into 16-tile segments, so the
+    # per-segment TMEM release and exact fixed-point segment sums run here
+    c = make_config("5s")
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"])
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision="split16",
+                slices=4, acc_flush_min=1, mixed_from=mixed_from)
+    g0 = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision="split16",
+                 slices=4, acc_flush_min=0, mixed_from=mixed_from)
+    err, err0 = _err(g, o), _err(g0, o)
+    print(f"5s split16 mixed_from={mixed_from}: segmented {err:.3e}, unsegmented {err0:.3e} (oracle n = {o.n})")
+    assert g["code"] == 0 and g["stats"]["converged"]
+    assert err <= MIXED_TOL and err0 <= MIXED_TOL
 
 
 @pytest.mark.parametrize("k", [2, 3])
