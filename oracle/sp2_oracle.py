@@ -20,6 +20,13 @@ What each function follows:
                               rule is a stated reading
   sp2 ....................... Algorithms 1 and 2
   homo_lumo_estimates ....... Section 4 Step 3 (reading; see the function)
+  sp2_trace_correcting ...... Section 1 (the original SP2: the polynomial of each
+                              iteration chosen from the trace) and Section 6 (the
+                              first run, without eigenvalue bounds)
+  bounds_from_estimates,
+  two_run ................... Section 6: run 1 trace-correcting, its Step 3
+                              estimates (with a stated margin) as the bounds of
+                              the SP2ACC run 2
   adjoint_sp2 ............... not in the paper: reverse-mode derivative of the
                               recursion for L = trace(D W)
 
@@ -463,6 +470,101 @@ def homo_lumo_estimates(res: SP2Result, n: int):
         if homo is not None and lumo is not None:
             break
     return homo, lumo
+
+
+# ----------------------------------------------------------------------------- Section 1 / 6: trace-correcting
+def sp2_trace_correcting(F: np.ndarray, nocc: int, tau: float = 0.0, stop: str = "parameterless",
+                         idem_tol: float = 1e-12, trunc: str = "frobenius", n_cap: int = 100,
+                         input_pattern=None, b: int = B, frobinf_part: int = FROBINF_PART) -> SP2Result:
+    """The SP2 expansion whose polynomial is chosen from the trace (Section 1:
+    the original SP2 algorithm; Section 6: the first run, where nothing is known
+    about the eigenvalues).  X_0 maps the occupied eigenvalues near 1 (Algorithm
+    1), so x^2 lowers the trace and 2x - x^2 raises it: p_i = 1 iff
+    trace(X~_{i-1}) > nocc (a tie takes 2x - x^2).  No acceleration (alpha_i =
+    1, n_min = 1), n_max = n_cap, the fixed truncation threshold tau for every
+    iteration; truncation, e_i, t_i and the stop tests as in Algorithm 2.
+    The returned schedule holds the p_i that were taken, so Step 3 estimates
+    follow the same reading as for SP2ACC."""
+    n = F.shape[0]
+    lmin, lmax = gershgorin_bounds(F)
+    sch = Schedule(lmin=lmin, lmax=lmax, n_max=n_cap, n_min=1)
+    sch.p.append(-1)
+    sch.alpha.append(float("nan"))
+    sch.tau = [float(tau)] * (n_cap + 1)
+    X = initial_matrix(F, lmin, lmax)
+    nb = (n + b - 1) // b
+    if input_pattern is None:
+        _, tl = upper_tiles(F, b)
+        input_pattern = {(i, j) for i, j, v in tl if v != 0.0 or i == j}
+    else:
+        input_pattern = set(input_pattern) | {(i, i) for i in range(nb)}
+    _, kept, dropped = truncate_select(X, tau, trunc, part=frobinf_part, pattern=input_pattern, b=b)
+    Xt = apply_drop(X, dropped, b)
+    kept_hist = [kept]
+    e, t = [], []
+    squares = 0
+    trip = 0
+    converged = False
+    n_out = None
+    for i in range(1, n_cap + 2):
+        if i <= n_cap:
+            p = 1 if float(np.trace(Xt)) > nocc else 0
+            sch.p.append(p)
+            sch.alpha.append(1.0)
+        S = Xt @ Xt
+        squares += 1
+        trip += _triplets(kept, nb)
+        R = Xt - S
+        e.append(float(np.sqrt(np.sum(R * R))))
+        t.append(float(np.trace(Xt) - np.trace(S)))
+        j = i - 1
+        if stop == "parameterless":
+            if j >= 2 and sch.p[j] != sch.p[j - 1] and e[j] > C_STOP * e[j - 2] ** 2:
+                converged, n_out = True, j
+                break
+        elif stop == "idempotency":
+            if e[j] < idem_tol:
+                converged, n_out = True, j
+                break
+        else:
+            raise ValueError(stop)
+        if i == n_cap + 1:
+            n_out = j
+            break
+        c0, c1, c2 = poly_coeffs(sch.p[i], 1.0)
+        Xi = c0 * np.eye(n) + c1 * Xt + c2 * S
+        pattern = product_pattern(kept, nb)
+        _, kept, dropped = truncate_select(Xi, tau, trunc, part=frobinf_part, pattern=pattern, b=b)
+        Xt = apply_drop(Xi, dropped, b)
+        kept_hist.append(kept)
+    res = SP2Result(D=Xt, n=n_out, e=e, t=t, sched=sch, kept=kept_hist, converged=converged,
+                    lmin=lmin, lmax=lmax, squares=squares, tile_triplets=trip)
+    res.estimates = homo_lumo_estimates(res, n)
+    return res
+
+
+def bounds_from_estimates(homo: float, lumo: float, lmin: float, lmax: float, margin: float = 0.1):
+    """Bounds for the second run from the first run's Step 3 estimates (Section
+    6).  The estimates are not bounds, so each moves away from the gap by
+    margin * (lumo - homo) (a stated reading; the paper gives no margin), and
+    stays inside the Gershgorin interval [lmin, lmax]."""
+    if homo is None or lumo is None or not (lumo > homo):
+        raise ValueError("no usable homo/lumo estimates")
+    d = margin * (lumo - homo)
+    return max(homo + d, lmin), min(lumo - d, lmax)
+
+
+def two_run(F: np.ndarray, nocc: int, tau1: float, tau: float = 0.0, gamma: float | None = None,
+            margin: float = 0.1, **kw):
+    """Section 6: run 1 is the trace-correcting expansion with the threshold
+    tau1; its Step 3 estimates, widened by the margin, are the homo/lumo bounds
+    of run 2, the SP2ACC expansion (tau or gamma as given).  Returns
+    (run1, run2, (homo_ub, lumo_lb))."""
+    pattern_kw = {k: kw[k] for k in ("input_pattern", "trunc", "frobinf_part", "n_cap") if k in kw}
+    r1 = sp2_trace_correcting(F, nocc, tau=tau1, **pattern_kw)
+    hub, llb = bounds_from_estimates(r1.estimates[0], r1.estimates[1], r1.lmin, r1.lmax, margin)
+    r2 = sp2(F, nocc, hub, llb, tau=tau, gamma=gamma, **kw)
+    return r1, r2, (hub, llb)
 
 
 # ----------------------------------------------------------------------------- adjoint

@@ -464,3 +464,54 @@ def test_adjoint_matches_daleckii_krein_closed_form():
             Gt[i, a] = Gt[a, i] = Wt[i, a] / (lam[i] - lam[a])
     ref = V @ Gt @ V.T
     assert np.linalg.norm(G - ref) <= 1e-6 * np.linalg.norm(ref)
+
+
+# ----------------------------------------------------------------- trace-correcting SP2, two runs
+def test_trace_correcting_reaches_eigenprojector():
+    # Section 1: the trace-correcting SP2 needs no eigenvalue bounds; at tau = 0
+    # it converges to D of Eq. (3)
+    c = make_config(1)
+    r = O.sp2_trace_correcting(c["F"], c["nocc"], tau=0.0, stop="idempotency")
+    assert r.converged and r.e[r.n] < 1e-12
+    assert np.linalg.norm(r.D - O.eig_projector(c["F"], c["nocc"])) < 1e-12
+    d = dense_gapped(70, 33, (-1.5, -0.2), (0.2, 1.5), seed=31)
+    r = O.sp2_trace_correcting(d["F"], d["nocc"], tau=0.0)
+    assert r.converged
+    assert np.linalg.norm(r.D - O.eig_projector(d["F"], d["nocc"])) < 1e-11
+
+
+def test_trace_correcting_choices_follow_the_eigenvalue_recursion():
+    # the same rule on the eigenvalues of X_0 as scalars: p_i = 1 iff the sum of
+    # the images exceeds nocc; compared while the trace is clearly off nocc
+    d = dense_gapped(90, 41, (-2.0, -0.1), (0.3, 1.7), seed=8)
+    r = O.sp2_trace_correcting(d["F"], d["nocc"], tau=0.0, stop="idempotency")
+    x = (r.lmax - d["eigenvalues"]) / (r.lmax - r.lmin)
+    compared = 0
+    for i in range(1, r.n + 1):
+        s = float(np.sum(x))
+        if abs(s - d["nocc"]) < 1e-8:
+            break
+        p = 1 if s > d["nocc"] else 0
+        assert r.sched.p[i] == p, i
+        compared += 1
+        x = O.poly_scalar(p, 1.0, x)
+    assert compared >= 10
+
+
+@pytest.mark.parametrize("key", [1, "2s"])
+def test_two_run_bounds_bracket_the_gap(key):
+    # Section 6: run 1 (trace-correcting) gives Step 3 estimates; widened by the
+    # margin they must be valid bounds (homo_ub >= homo, lumo_lb <= lumo) for
+    # the SP2ACC run 2, which then converges in fewer iterations than run 1
+    c = make_config(key)
+    F = c["F"] if isinstance(c["F"], np.ndarray) else to_dense(c["F"])
+    tau1 = 0.0 if key == 1 else 1e-5
+    kw = dict(stop=c["stop"])
+    r1, r2, (hub, llb) = O.two_run(F, c["nocc"], tau1, tau=c["tau"], **kw)
+    ev = np.linalg.eigvalsh(F)
+    assert hub >= ev[c["nocc"] - 1] and llb <= ev[c["nocc"]]
+    assert r2.converged and r2.n < r1.n
+    if key == 1:
+        assert np.linalg.norm(r2.D - O.eig_projector(F, c["nocc"])) < 1e-12
+    with pytest.raises(ValueError):
+        O.bounds_from_estimates(None, 0.5, -1.0, 1.0)
