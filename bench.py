@@ -1,12 +1,14 @@
 #!/usr/bin/env python
 """SP2 time-to-D and effective TFLOP/s on one GB300 (whole SP2ACC expansion per step).
 
-Workload (default): the water-like Fock matrix with 1000 molecules, N = 24000,
-tile b = 32, tau = 1e-6, Frobenius truncation, parameterless stop.  It is a
-seeded synthetic stand-in for the paper's HF/3-21G water clusters.
-The headline path is the tcgen05 tensor-core square on four FP16 slices (the
-FP64 GPU path is timed once on the same workload for comparison, and the
-difference of the two D's is reported).
+Workload (default): the precision form of the water-like recipe -- 8000
+molecules of 24 basis functions, N = 192000, tile b = 32, tau = 1e-5,
+Frobenius truncation, parameterless stop.  It is a seeded synthetic stand-in
+for the paper's HF/3-21G water clusters.  The headline path is the mixed one:
+tcgen05 tensor-core squares on four FP16 slices, with traces, norms, the
+polynomial choice and the stop test in FP64.  The FP64 GPU path is timed once
+on the same workload, and the difference of the two D's is reported (the
+metric compares the two paths at ||D - D_FP64||_F <= 1e-6).
 A step is one full pass of the method: sp2_create from the device-resident F
 (Gershgorin bounds, schedule, X_0), then sp2_run (every iteration's symbolic
 square, tile products with the fused epilogue, reductions, stop test,
@@ -18,7 +20,8 @@ With --gpus N > 1 each rank runs an independent replica (the path runs on one
 GPU; value sums all ranks' flops over the slowest rank's time).
 
 --impl reference times the CPU oracle (plain numpy FP64) on a bounded sample of
-the same recipe (101 molecules, N = 2424) on this host's cores.
+the same recipe (203 molecules, N = 4872, tau = 1e-5 for the default workload)
+on this host's cores.
 """
 from __future__ import annotations
 
@@ -37,16 +40,19 @@ sys.path.insert(0, str(ROOT))
 
 METRIC = "SP2 time-to-D & eff. TFLOP/s, mixed vs FP64 GPU path at ||D-Dref||_F<=1e-6"
 WORKLOADS = {
-    "water24k": dict(key=2, desc="water-like, 1000 molecules x 24 basis functions, N=24000, b=32, tau=1e-6, "
-                               "Frobenius truncation, parameterless stop"),
-    "water2k": dict(key="2s", desc="water-like, 101 molecules, N=2424, b=32, tau=1e-6"),
-    "water9k": dict(key="2m", desc="water-like, 400 molecules, N=9600, b=32, tau=1e-6"),
-    "helix128k": dict(key=4, desc="helix-like chain, 2000 residues x 64, N=128000, tau=1e-6"),
-    "water192k": dict(key=3, desc="water-like, 8000 molecules x 24, N=192000, b=32, tau=1e-5"),
-    "dense16k": dict(key=5, desc="dense N=16384, gap 0.05, tau=0, idempotency stop 1e-12"),
-    "dense512": dict(key=1, desc="dense N=512, tau=0, idempotency stop 1e-12"),
+    "water192k": dict(key=3, sample="3s",
+                      desc="water-like, 8000 molecules x 24 basis functions, N=192000, b=32, tau=1e-5, "
+                           "Frobenius truncation, parameterless stop (the precision form)"),
+    "water24k": dict(key=2, sample="2s",
+                     desc="water-like, 1000 molecules x 24 basis functions, N=24000, b=32, tau=1e-6, "
+                          "Frobenius truncation, parameterless stop"),
+    "water2k": dict(key="2s", sample="2s", desc="water-like, 101 molecules, N=2424, b=32, tau=1e-6"),
+    "water9k": dict(key="2m", sample="2s", desc="water-like, 400 molecules, N=9600, b=32, tau=1e-6"),
+    "helix128k": dict(key=4, sample="4s", desc="helix-like chain, 2000 residues x 64, N=128000, tau=1e-6"),
+    "dense16k": dict(key=5, sample="5s", desc="dense N=16384, gap 0.05, tau=0, idempotency stop 1e-12"),
+    "dense512": dict(key=1, sample=1, desc="dense N=512, tau=0, idempotency stop 1e-12"),
 }
-CPU_SAMPLE_KEY = "2s"
+DEFAULT_WORKLOAD = "water192k"
 PEAK_FP64_TFLOPS = 1.25   # GB300 FP64 nominal (no FP64 tensor path on this chip)
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, mean bytes per launch) of the
@@ -123,21 +129,24 @@ def dist_env():
     return rank, world, local
 
 
-def cpu_oracle_sample() -> dict:
+def cpu_oracle_sample(workload: str) -> dict:
     """The CPU oracle as it stands on a bounded sample of the same recipe."""
+    import numpy as np
     import oracle.sp2_oracle as O
-    from synth import make_config, to_dense
-    c = make_config(CPU_SAMPLE_KEY)
-    F = to_dense(c["F"])
-    pattern = set(zip(c["F"].brow.tolist(), c["F"].bcol.tolist()))
+    from synth import from_dense, make_config, to_dense
+    key = WORKLOADS[workload]["sample"]
+    c = make_config(key)
+    Fb = c["F"] if not isinstance(c["F"], np.ndarray) else from_dense(c["F"])
+    F = to_dense(Fb)
+    pattern = set(zip(Fb.brow.tolist(), Fb.bcol.tolist()))
     t0 = time.perf_counter()
-    r = O.sp2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], tau=c["tau"], input_pattern=pattern)
+    r = O.sp2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], tau=c["tau"], stop=c["stop"], input_pattern=pattern)
     dt = time.perf_counter() - t0
     flops = 2.0 * 32 ** 3 * r.tile_triplets
     return {"value": flops / dt / 1e12, "unit": "TFLOP/s", "seconds": dt, "flops": flops, "iterations": r.n,
             "cores": len(os.sched_getaffinity(0)), "kind": "oracle",
-            "sample": f"full SP2ACC run of the oracle (dense numpy FP64) on the same water-like recipe at "
-                      f"101 molecules (N={F.shape[0]}) instead of 1000"}
+            "sample": f"one full SP2ACC run of the oracle (dense numpy FP64, BLAS on all host cores) on the "
+                      f"same recipe reduced to config '{key}' (N={F.shape[0]}, tau={c['tau']:g})"}
 
 
 def run_reference(args):
@@ -145,15 +154,16 @@ def run_reference(args):
     if rank != 0:
         return 0
     for _ in range(args.warmup):
-        cpu_oracle_sample()
-    samples = [cpu_oracle_sample() for _ in range(args.steps)]
+        cpu_oracle_sample(args.workload)
+    samples = [cpu_oracle_sample(args.workload) for _ in range(args.steps)]
     tot_flops = sum(s["flops"] for s in samples)
     tot_s = sum(s["seconds"] for s in samples)
     v = tot_flops / tot_s / 1e12
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "TFLOP/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * tot_s / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": samples[0]["sample"], "l2": "n/a (CPU)"},
+            "config": {"workload": WORKLOADS[args.workload]["desc"] + "; timed on the CPU sample: " +
+                              samples[0]["sample"], "l2": "n/a (CPU)"},
             "cpu_baseline": {"value": v, "unit": "TFLOP/s", "cores": samples[0]["cores"], "kind": "oracle",
                              "sample": samples[0]["sample"]},
             "e2e": {"value": v, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -194,7 +204,7 @@ def main(argv=None) -> int:
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="water24k", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="split16", choices=["fp64", "split16"])
     ap.add_argument("--slices", type=int, default=4)
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the timed FP64 reference run")
@@ -370,7 +380,7 @@ def main(argv=None) -> int:
         "roofline": roof, "clocks": clk, "gpu_launches": int(launches), "e2e": e2e,
     }
     if not args.no_cpu_baseline and world == 1:
-        cb = cpu_oracle_sample()
+        cb = cpu_oracle_sample(args.workload)
         line["cpu_baseline"] = {k: cb[k] for k in ("value", "unit", "cores", "kind", "sample")}
     print(json.dumps(line), flush=True)
     if world > 1:

@@ -59,7 +59,11 @@ extern "C" {
 #define SP2_MAX_ITER 128
 
 /* ---------------------------------------------------------------- enums */
-enum sp2_mode      { SP2_MODE_SP2 = 0, SP2_MODE_SP2ACC = 1 };
+/* Polynomial choice: SP2 and SP2ACC follow the schedule of Section 4 Step 1
+ * (homo/lumo bounds required); TRACE is the trace-correcting expansion of
+ * Section 1 (p_i = 1 iff trace(X~_{i-1}) > nocc, alpha_i = 1, no bounds needed:
+ * the first run of Section 6). */
+enum sp2_mode      { SP2_MODE_SP2 = 0, SP2_MODE_SP2ACC = 1, SP2_MODE_TRACE = 2 };
 /* Stop tests: Algorithm 2's parameterless criterion, or e_j < idem_tol. */
 enum sp2_stop      { SP2_STOP_PARAMETERLESS = 0, SP2_STOP_IDEMPOTENCY = 1 };
 /* Truncation norm: Frobenius (Section 2) or Frob-Inf (Section 3, Eq. (13)). */
@@ -169,7 +173,10 @@ int sp2_default_params(sp2_params* p);
  * (p_i, alpha_i, n_min, n_max, tau_i) from homo_ub >= lambda_homo and
  * lumo_lb <= lambda_lumo, form X_0 = (lmax I - F)/(lmax - lmin) and its
  * truncation X~_0.  tau is the truncation threshold of every iteration
- * (ignored when params->gamma > 0).  nocc is used for reporting only.
+ * (ignored when params->gamma > 0).  nocc is used for reporting only, except
+ * in SP2_MODE_TRACE, where it steers the polynomial choice; that mode takes no
+ * bounds (homo_ub and lumo_lb are ignored and may be NaN), n_max is n_max_cap,
+ * and gamma must be 0 (Eq. (7) needs a gap bound).
  * Errors: INVALID_ARG, PATTERN, NONFINITE, BOUNDS, OOM, CUDA.  On error *out is NULL. */
 int sp2_create(const sp2_bsr* F, int64_t nocc, double homo_ub, double lumo_lb, double tau,
                const sp2_params* params, const sp2_allocator* alloc, void* cuda_stream,
@@ -192,6 +199,16 @@ int sp2_create_dense(const double* F, int64_t n, int64_t ld, int32_t on_device, 
  * fires, then estimate homo/lumo.  Returns SP2_OK, SP2_ERR_NOT_CONVERGED (D is
  * the last iterate and readable), or an error.  stats may be NULL. */
 int sp2_run(sp2_ctx* ctx, sp2_stats* stats);
+
+/* Section 6's second run: homo/lumo bounds from the Step 3 estimates of the
+ * last sp2_run of ctx (typically a SP2_MODE_TRACE run).  The estimates are not
+ * bounds, so each moves away from the gap by margin * (lumo_est - homo_est)
+ * (the paper gives no margin; 0 <= margin < 0.5) and stays inside the
+ * Gershgorin interval [lmin, lmax]:
+ *   *homo_ub = max(homo_est + d, lmin),  *lumo_lb = min(lumo_est - d, lmax).
+ * Errors: INVALID_ARG, STATE (no run, or the run gave no estimate of one side,
+ * or lumo_est <= homo_est). */
+int sp2_estimate_bounds(const sp2_ctx* ctx, double margin, double* homo_ub, double* lumo_lb);
 
 /* Borrowed device view of D (tile arrays owned by ctx, valid until the next
  * sp2_run, sp2_backward or sp2_destroy).  view->on_device = 1. */

@@ -560,7 +560,8 @@ def two_run(F: np.ndarray, nocc: int, tau1: float, tau: float = 0.0, gamma: floa
     tau1; its Step 3 estimates, widened by the margin, are the homo/lumo bounds
     of run 2, the SP2ACC expansion (tau or gamma as given).  Returns
     (run1, run2, (homo_ub, lumo_lb))."""
-    pattern_kw = {k: kw[k] for k in ("input_pattern", "trunc", "frobinf_part", "n_cap") if k in kw}
+    pattern_kw = {k: kw[k] for k in ("input_pattern", "trunc", "frobinf_part", "n_cap", "stop", "idem_tol")
+                  if k in kw}
     r1 = sp2_trace_correcting(F, nocc, tau=tau1, **pattern_kw)
     hub, llb = bounds_from_estimates(r1.estimates[0], r1.estimates[1], r1.lmin, r1.lmax, margin)
     r2 = sp2(F, nocc, hub, llb, tau=tau, gamma=gamma, **kw)

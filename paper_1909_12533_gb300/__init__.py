@@ -27,7 +27,7 @@ ERRORS = {
     -9: "SP2_ERR_STATE", -10: "SP2_ERR_CAPACITY", -11: "SP2_ERR_TOO_LARGE", -12: "SP2_ERR_RANGE",
 }
 NOT_CONVERGED = -7
-MODES = {"sp2": 0, "sp2acc": 1}
+MODES = {"sp2": 0, "sp2acc": 1, "trace": 2}
 STOPS = {"parameterless": 0, "idempotency": 1}
 TRUNCS = {"frobenius": 0, "frobinf": 1}
 PRECISIONS = {"fp64": 0, "split16": 1}
@@ -69,6 +69,7 @@ _SIGS = [
     ("sp2_create_dense", c_int32, [c_void_p, c_int64, c_int64, c_int32, c_int64, c_double, c_double, c_double,
                                    POINTER(sp2_params), POINTER(sp2_allocator), c_void_p, POINTER(c_void_p)]),
     ("sp2_run", c_int32, [c_void_p, POINTER(sp2_stats)]),
+    ("sp2_estimate_bounds", c_int32, [c_void_p, c_double, POINTER(c_double), POINTER(c_double)]),
     ("sp2_get_D", c_int32, [c_void_p, POINTER(sp2_bsr)]),
     ("sp2_copy_D", c_int32, [c_void_p, c_void_p, c_void_p, c_void_p, c_int64, c_int32, POINTER(c_int64)]),
     ("sp2_copy_D_dense", c_int32, [c_void_p, c_void_p, c_int64, c_int32]),
@@ -220,6 +221,17 @@ def sp2_run(ctx) -> tuple[int, sp2_stats]:
     if rc not in (SP2_OK, NOT_CONVERGED):
         raise SP2Error(rc, "sp2_run")
     return rc, st
+
+
+def sp2_estimate_bounds(ctx, margin: float = 0.1) -> tuple[float, float]:
+    """(homo_ub, lumo_lb) for a second run from the Step 3 estimates of the
+    last run of ctx, each moved away from the gap by margin * estimated gap."""
+    h = c_double()
+    l = c_double()
+    rc = load().sp2_estimate_bounds(ctx, float(margin), byref(h), byref(l))
+    if rc != SP2_OK:
+        raise SP2Error(rc, "sp2_estimate_bounds")
+    return h.value, l.value
 
 
 def sp2_get_D(ctx) -> sp2_bsr:
@@ -440,6 +452,27 @@ def run(F, nocc, homo_ub, lumo_lb, tau, stream=None, **params):
     finally:
         ctx.close()
     return D, st
+
+
+def run_two_pass(F, nocc, tau1, tau, margin: float = 0.1, stream=None, first=None, **params):
+    """Section 6's protocol when no eigenvalue bounds are known: run 1 is the
+    trace-correcting expansion (mode "trace") with the threshold tau1, its Step 3
+    estimates widened by ``margin`` (sp2_estimate_bounds) are the homo/lumo
+    bounds of run 2, the SP2ACC expansion with tau (and **params).  ``first``:
+    extra parameters of run 1 only.  Returns (D, stats of run 2, stats of run 1,
+    (homo_ub, lumo_lb)) with D as ``run`` returns it."""
+    p1 = dict(params)
+    p1.pop("gamma", None)
+    p1.update(first or {})
+    p1["mode"] = "trace"
+    ctx = SP2(F, nocc, float("nan"), float("nan"), tau1, stream=stream, **p1)
+    try:
+        st1 = ctx.run()
+        bounds = sp2_estimate_bounds(ctx.ctx, margin)
+    finally:
+        ctx.close()
+    D, st2 = run(F, nocc, bounds[0], bounds[1], tau, stream=stream, **params)
+    return D, st2, st1, bounds
 
 
 def header_functions() -> list[str]:

@@ -67,6 +67,33 @@ __global__ void __launch_bounds__(256) k_place(const int32_t* __restrict__ srowp
   }
 }
 
+// Trace of the kept diagonal tiles of a tile set (the trace-correcting choice
+// of Section 1 needs trace(X~) before the next product): rows I whose first
+// tile is (I, I) and kept (keep == nullptr: all kept) add the real part of the
+// tile's diagonal.  One CTA, fixed summation order (deterministic).
+constexpr int TRACE_T = 1024;
+__global__ void __launch_bounds__(TRACE_T)
+    k_trace_kept(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ bcol,
+                 const int32_t* __restrict__ slot, const int32_t* __restrict__ keep,
+                 const double* __restrict__ pool, int nb, int64_t n, double* out) {
+  __shared__ double red[TRACE_T];
+  double acc = 0.0;
+  for (int I = threadIdx.x; I < nb; I += TRACE_T) {
+    const int t = rowptr[I];
+    if (t < rowptr[I + 1] && bcol[t] == I && (!keep || keep[t])) {
+      const double* x = pool + (int64_t)(slot ? slot[t] : t) * TE;
+      for (int r = 0; r < TB && (int64_t)I * TB + r < n; ++r) acc += x[r * (TB + 1)];
+    }
+  }
+  red[threadIdx.x] = acc;
+  __syncthreads();
+  for (int h = TRACE_T / 2; h > 0; h >>= 1) {
+    if (threadIdx.x < h) red[threadIdx.x] += red[threadIdx.x + h];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 __global__ void k_iota(int32_t* p, int64_t n) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i < n) p[i] = (int32_t)i;
@@ -80,6 +107,13 @@ cudaError_t launch_place(const TileSet& src, const double* spool, const TileSet&
                          int sym_diag, cudaStream_t st) {
   if (dst.nnzb == 0) return cudaSuccess;
   { ++g_launches; k_place<<<(unsigned)dst.nnzb, 256, 0, st>>>(src.rowptr, src.bcol, src.slot, spool, dst.brow, dst.bcol, dst.slot, dpool, scale, sym_diag); }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_kept(const TileSet& s, const int32_t* keep, const double* pool, int nb, int64_t n,
+                              double* out, cudaStream_t st) {
+  ++g_launches;
+  k_trace_kept<<<1, TRACE_T, 0, st>>>(s.rowptr, s.bcol, s.slot, keep, pool, nb, n, out);
   return cudaGetLastError();
 }
 

@@ -133,6 +133,24 @@ Schedule make_schedule(double lmin, double lmax, double homo_ub, double lumo_lb,
   return s;
 }
 
+// Trace-correcting expansion (Section 1): no bounds, so no schedule ahead of
+// time -- p_i is chosen from trace(X~_{i-1}) during the run, alpha_i = 1,
+// n_min = 1, n_max = the cap, tau_i = tau.
+Schedule make_schedule_trace(double lmin, double lmax, double tau, int n_cap) {
+  Schedule s;
+  s.lmin = lmin;
+  s.lmax = lmax;
+  s.n_max = n_cap;
+  s.n_min = 1;
+  s.p.assign(n_cap + 1, -1);
+  s.alpha.assign(n_cap + 1, 1.0);
+  s.alpha[0] = NAN;
+  s.tau.assign(n_cap + 1, tau);
+  s.vhi.assign(n_cap + 1, NAN);
+  s.olo.assign(n_cap + 1, NAN);
+  return s;
+}
+
 void coeffs(int p, double a, double& c0, double& c1, double& c2) {
   if (p == 1) {
     c0 = (1.0 - a) * (1.0 - a);
@@ -339,7 +357,7 @@ struct sp2_ctx {
   std::vector<Rec> recs;
   std::vector<Buf> seg;
   Buf ident, fpB_bits, fpB_rowptr, fpB_col, fpB_ref, gpool[2], w_brow, w_bcol, w_rowptr, w_pool, dF;
-  Buf amax;
+  Buf amax, trbuf;
   FullPattern fpB;
   double backward_ms = 0.0;
   HostBlock* hb = nullptr;
@@ -362,7 +380,7 @@ struct sp2_ctx {
                   &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &opx.sbits,
                   &opx.cnt, &opx.spos, &opx.index, &opx.head, &opx.data, &opy.sbits, &opy.cnt, &opy.spos,
                   &opy.index, &opy.head, &opy.data, &sflag, &spos, &slist, &errflag, &scount, &tcscratch, &redwork, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
-                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax};
+                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax, &trbuf};
     for (Buf* b : all) bufs.push_back(b);
   }
 
@@ -484,10 +502,6 @@ void adopt_X(sp2_ctx* c, TileSet t, int64_t nnzb, int set) {
   c->ck(launch_rowptr_from_brow(c->X.brow, c->X.nnzb, c->nb, c->X.rowptr, c->st), "rowptr");
 }
 
-void truncate_into_X(sp2_ctx* c, const TileSet& in, const double* n2, double tau) {
-  TileSet t = truncate_launch(c, in, n2, tau, 0);
-  adopt_X(c, t, read_count(c, c->dcnt.as<int32_t>()), 0);
-}
 
 void free_recs(sp2_ctx* c) {
   for (Rec& r : c->recs)
@@ -770,13 +784,18 @@ namespace {
 int check_create_args(int64_t n, double homo_ub, double lumo_lb, double tau, const sp2_params* params,
                       const sp2_allocator* alloc, sp2_params& prm) {
   if (n <= 0) return SP2_ERR_INVALID_ARG;
-  if (!std::isfinite(homo_ub) || !std::isfinite(lumo_lb) || !std::isfinite(tau) || tau < 0.0)
-    return SP2_ERR_INVALID_ARG;
-  if (!(homo_ub < lumo_lb)) return SP2_ERR_BOUNDS;
-  if (alloc && (!alloc->alloc || !alloc->free)) return SP2_ERR_INVALID_ARG;
   sp2_default_params(&prm);
   if (params) prm = *params;
-  if (prm.mode != SP2_MODE_SP2 && prm.mode != SP2_MODE_SP2ACC) return SP2_ERR_INVALID_ARG;
+  if (prm.mode != SP2_MODE_SP2 && prm.mode != SP2_MODE_SP2ACC && prm.mode != SP2_MODE_TRACE)
+    return SP2_ERR_INVALID_ARG;
+  if (!std::isfinite(tau) || tau < 0.0) return SP2_ERR_INVALID_ARG;
+  if (prm.mode == SP2_MODE_TRACE) {
+    if (prm.gamma != 0.0) return SP2_ERR_INVALID_ARG;   // Eq. (7) needs a gap bound
+  } else {
+    if (!std::isfinite(homo_ub) || !std::isfinite(lumo_lb)) return SP2_ERR_INVALID_ARG;
+    if (!(homo_ub < lumo_lb)) return SP2_ERR_BOUNDS;
+  }
+  if (alloc && (!alloc->alloc || !alloc->free)) return SP2_ERR_INVALID_ARG;
   if (prm.stop != SP2_STOP_PARAMETERLESS && prm.stop != SP2_STOP_IDEMPOTENCY) return SP2_ERR_INVALID_ARG;
   if (!(prm.fp64_tail >= 0.0) || !std::isfinite(prm.fp64_tail)) return SP2_ERR_INVALID_ARG;
   if (prm.acc_flush_min < 0) return SP2_ERR_INVALID_ARG;
@@ -861,10 +880,15 @@ void finish_create(sp2_ctx* c, int64_t nnzb) {
   c->ck(cudaMemcpyAsync(c->h_d2, c->d2.p, 16, cudaMemcpyDeviceToHost, c->st), "d2h");
   c->sync();
   const double lmin = c->h_d2[0], lmax = c->h_d2[1];
-  if (!(lmin <= c->homo_ub) || !(c->lumo_lb <= lmax) || !(lmax > lmin)) throw Fail{SP2_ERR_BOUNDS};
   const sp2_params& prm = c->prm;
-  c->sch = make_schedule(lmin, lmax, c->homo_ub, c->lumo_lb, c->tau, prm.gamma, prm.mode == SP2_MODE_SP2ACC,
-                         prm.delta_acc, prm.n_max_cap);
+  if (prm.mode == SP2_MODE_TRACE) {
+    if (!(lmax > lmin)) throw Fail{SP2_ERR_BOUNDS};
+    c->sch = make_schedule_trace(lmin, lmax, c->tau, prm.n_max_cap);
+  } else {
+    if (!(lmin <= c->homo_ub) || !(c->lumo_lb <= lmax) || !(lmax > lmin)) throw Fail{SP2_ERR_BOUNDS};
+    c->sch = make_schedule(lmin, lmax, c->homo_ub, c->lumo_lb, c->tau, prm.gamma, prm.mode == SP2_MODE_SP2ACC,
+                           prm.delta_acc, prm.n_max_cap);
+  }
   fill_stats_sched(c);
   c->stats.status = SP2_OK;
   c->stats.homo_est = c->stats.lumo_est = NAN;
@@ -975,6 +999,7 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
   try {
     sp2_stats& S = c->stats;
     const Schedule& sch = c->sch;
+    if (c->prm.mode == SP2_MODE_TRACE) std::fill(c->sch.p.begin() + 1, c->sch.p.end(), -1);   // chosen below
     fill_stats_sched(c);
     S.converged = 0;
     S.squares = 0;
@@ -1000,7 +1025,20 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
                     c->p_n2.as<double>(), c->st),
           "x0");
     c->cur = 0;
-    truncate_into_X(c, c->F, c->p_n2.as<double>(), sch.tau[0]);
+    const bool trace_mode = c->prm.mode == SP2_MODE_TRACE;
+    {
+      TileSet t0 = truncate_launch(c, c->F, c->p_n2.as<double>(), sch.tau[0], 0);
+      if (trace_mode) {
+        // trace(X~_0) for the first choice (X_0's tiles in F's order, values in pool[0])
+        c->ensure(c->trbuf, 16);
+        c->ck(launch_trace_kept(c->F, c->keep.as<int32_t>(), c->pool[0].as<double>(), c->nb, c->n,
+                                c->trbuf.as<double>(), c->st),
+              "trace");
+        c->ck(cudaMemcpyAsync(c->h_d2 + 1, c->trbuf.p, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
+      }
+      adopt_X(c, t0, read_count(c, c->dcnt.as<int32_t>()), 0);
+    }
+    double tr_cur = trace_mode ? c->h_d2[1] : 0.0;   // trace(X~_{i-1}) in trace mode
     S.nnzb_hist[0] = c->X.nnzb;
     c->tail_from = 0;
     free_recs(c);
@@ -1038,7 +1076,15 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       ensure_partials(c, nout);
       int p = 1;
       double a = 1.0;
-      if (i <= sch.n_max) { p = sch.p[i]; a = sch.alpha[i]; }
+      if (i <= sch.n_max) {
+        if (trace_mode) {
+          // Section 1: x^2 lowers the trace, 2x - x^2 raises it (ties: 2x - x^2)
+          c->sch.p[i] = tr_cur > (double)c->nocc ? 1 : 0;
+          S.p[i] = c->sch.p[i];
+        }
+        p = sch.p[i];
+        a = sch.alpha[i];
+      }
       double c0, c1, c2;
       coeffs(p, a, c0, c1, c2);
       SquareArgs sa;
@@ -1065,6 +1111,13 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       const bool more = i <= sch.n_max;
       TileSet next;
       if (more) next = truncate_launch(c, c->out, c->p_n2.as<double>(), sch.tau[i], 1 - c->xset);
+      if (more && trace_mode) {
+        // trace(X~_i) for the next choice: the kept diagonal tiles of the output
+        c->ck(launch_trace_kept(c->out, c->keep.as<int32_t>(), c->pool[nxt].as<double>(), c->nb, c->n,
+                                c->trbuf.as<double>(), c->st),
+              "trace");
+        c->ck(cudaMemcpyAsync(c->h_d2 + 1, c->trbuf.p, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
+      }
       // one host round trip per step: scalars, error flags, kept-tile count
       c->ck(cudaMemcpyAsync(c->h_sc, c->dsc.p, sizeof(StepScalars), cudaMemcpyDeviceToHost, c->st), "d2h");
       c->ck(cudaMemcpyAsync(c->h_cnt + 2, c->errflag.p, 8, cudaMemcpyDeviceToHost, c->st), "d2h");
@@ -1119,6 +1172,7 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       if (stop) { n_out = j; converged = true; break; }
       if (!more) { n_out = j; break; }
       adopt_X(c, next, c->h_cnt[0], 1 - c->xset);
+      if (trace_mode) tr_cur = c->h_d2[1];
       c->cur = nxt;
       S.nnzb_hist[i] = c->X.nnzb;
       record(c, i);
@@ -1156,6 +1210,16 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
   c->stats.status = status;
   if (stats_out) *stats_out = c->stats;
   return status;
+}
+
+int sp2_estimate_bounds(const sp2_ctx* c, double margin, double* homo_ub, double* lumo_lb) {
+  if (!c || !homo_ub || !lumo_lb || !(margin >= 0.0) || !(margin < 0.5)) return SP2_ERR_INVALID_ARG;
+  const sp2_stats& s = c->stats;
+  if (!c->ran || (s.have_estimates & 3) != 3 || !(s.lumo_est > s.homo_est)) return SP2_ERR_STATE;
+  const double d = margin * (s.lumo_est - s.homo_est);
+  *homo_ub = std::max(s.homo_est + d, s.lmin);
+  *lumo_lb = std::min(s.lumo_est - d, s.lmax);
+  return SP2_OK;
 }
 
 int sp2_get_D(sp2_ctx* c, sp2_bsr* view) {

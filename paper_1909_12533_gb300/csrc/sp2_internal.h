@@ -113,6 +113,9 @@ cudaError_t launch_copy_index(const TileSet& s, int32_t* brow, int32_t* bcol, cu
 cudaError_t launch_place(const TileSet& src, const double* spool, const TileSet& dst, double* dpool, double scale,
                          int sym_diag, cudaStream_t st);
 cudaError_t launch_iota(int32_t* p, int64_t n, cudaStream_t st);
+// *out = trace of the kept diagonal tiles of s (s needs rowptr; keep may be nullptr)
+cudaError_t launch_trace_kept(const TileSet& s, const int32_t* keep, const double* pool, int nb, int64_t n,
+                              double* out, cudaStream_t st);
 
 // dense.cu: dense row-major matrix <-> upper tiles
 // flag[I * nb + J] = 1 for every diagonal tile and every nonzero tile with J > I

@@ -210,3 +210,70 @@ def test_homo_lumo_estimates_near_exact_eigenvalues_plain_sp2():
     assert st["have_estimates"] == 3
     assert abs(st["homo_est"] - ev[c["nocc"] - 1]) < 0.02
     assert abs(st["lumo_est"] - ev[c["nocc"]]) < 0.02
+
+
+# ----------------------------------------------------------------- trace-correcting SP2 (Section 1, 6)
+def _run_oracle_trace(c, tau, **kw):
+    import oracle.sp2_oracle as O
+    from tests.helpers import as_blocks
+    Fb = as_blocks(c["F"])
+    return O.sp2_trace_correcting(to_dense(Fb), c["nocc"], tau=tau, input_pattern=set(zip(Fb.brow.tolist(),
+                                                                                           Fb.bcol.tolist())), **kw)
+
+
+@pytest.mark.parametrize("key", [1, "2s", "4s"])
+def test_trace_correcting_matches_oracle(key):
+    # no bounds passed (NaN): the polynomial of each iteration comes from trace(X~)
+    c = _case(key)
+    g = run_gpu(c["F"], c["nocc"], float("nan"), float("nan"), c["tau"], stop=c["stop"], mode="trace")
+    o = _run_oracle_trace(c, c["tau"], stop=c["stop"])
+    st = g["stats"]
+    assert g["code"] == 0 and st["converged"] and o.converged
+    assert st["n"] == o.n
+    assert st["p"][1:o.n + 1] == o.sched.p[1:o.n + 1]
+    assert all(a == 1.0 for a in st["alpha"][1:o.n + 1])
+    assert st["tile_triplets"] == o.tile_triplets
+    np.testing.assert_allclose(st["e"], o.e, rtol=1e-8, atol=1e-12)
+    assert st["nnzb_hist"][: o.n + 1] == [len(k) for k in o.kept[: o.n + 1]]
+    assert np.linalg.norm(g["D"] - o.D) <= 1e-10
+    oh, ol = o.estimates
+    if oh is not None:
+        assert abs(st["homo_est"] - oh) <= 1e-8 * max(1.0, abs(oh))
+    if ol is not None:
+        assert abs(st["lumo_est"] - ol) <= 1e-8 * max(1.0, abs(ol))
+
+
+@pytest.mark.parametrize("key", [1, "2s", "4s"])
+def test_two_run_protocol_matches_oracle(key):
+    # Section 6: run 1 trace-correcting, run 2 SP2ACC with run 1's estimates
+    # widened by 0.1 of the estimated gap; both sides give the same bounds and D
+    import oracle.sp2_oracle as O
+    import paper_1909_12533_gb300 as sp2
+    from tests.helpers import as_blocks
+    c = _case(key)
+    Fb = as_blocks(c["F"])
+    tau1 = 1e-5 if c["tau"] > 0 else 0.0
+    (brow, bcol, val), st2, st1, (hub, llb) = sp2.run_two_pass(Fb, c["nocc"], tau1, c["tau"], margin=0.1,
+                                                              stop=c["stop"])
+    r1, r2, (ohub, ollb) = O.two_run(to_dense(Fb), c["nocc"], tau1, tau=c["tau"], margin=0.1, stop=c["stop"],
+                                      input_pattern=set(zip(Fb.brow.tolist(), Fb.bcol.tolist())))
+    assert st1["n"] == r1.n and st2["n"] == r2.n
+    assert abs(hub - ohub) <= 1e-8 and abs(llb - ollb) <= 1e-8
+    D = to_dense(BlockSparse(n=Fb.n, brow=brow, bcol=bcol, val=val))
+    assert np.linalg.norm(D - r2.D) <= 1e-10
+    # run 2 against SP2ACC with the recipe's own (Weyl) bounds: iteration counts
+    g = run_gpu(Fb, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"])
+    print(f"config {key}: run 1 (trace) n = {st1['n']}, run 2 (SP2ACC, estimated bounds "
+          f"[{hub:.4f}, {llb:.4f}]) n = {st2['n']}, SP2ACC with the recipe's bounds "
+          f"[{c['homo_ub']:.4f}, {c['lumo_lb']:.4f}] n = {g['stats']['n']}")
+
+
+def test_trace_mode_rejects_gamma_and_accepts_nan_bounds():
+    import paper_1909_12533_gb300 as sp2
+    d = dense_gapped(64, 32, (-1.0, -0.5), (0.5, 1.0), seed=5)
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.SP2(from_dense(d["F"]), 32, float("nan"), float("nan"), 0.0, mode="trace", gamma=1e-3)
+    assert e.value.code == -1
+    with pytest.raises(sp2.SP2Error) as e:
+        sp2.SP2(from_dense(d["F"]), 32, float("nan"), float("nan"), 0.0)   # NaN bounds need trace mode
+    assert e.value.code == -1
