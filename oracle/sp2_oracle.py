@@ -19,6 +19,7 @@ What each function follows:
                               and Section 3 (Frob-Inf norm, Eq. (13)); selection
                               rule is a stated reading
   sp2 ....................... Algorithms 1 and 2
+  triplets_general .......... Section 5 (general storage: both triangles computed)
   homo_lumo_estimates ....... Section 4 Step 3 (reading; see the function)
   sp2_trace_correcting ...... Section 1 (the original SP2: the polynomial of each
                               iteration chosen from the trace) and Section 6 (the
@@ -342,6 +343,17 @@ def _triplets(kept, nb: int) -> int:
         A[j, i] = 1
     C = A @ A
     return int(np.triu(C).sum())
+
+
+def triplets_general(kept, nb: int) -> int:
+    """Number of (I, J, K) over the whole square, both triangles, with X~_IK and
+    X~_KJ stored: the tile products of the square in general storage (Section 5:
+    the general-matrix implementation stores and computes both triangles)."""
+    A = np.zeros((nb, nb), dtype=np.int64)
+    for i, j in kept:
+        A[i, j] = 1
+        A[j, i] = 1
+    return int((A @ A).sum())
 
 
 def sp2(F: np.ndarray, nocc: int, homo_ub: float, lumo_lb: float, tau: float = 0.0,

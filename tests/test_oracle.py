@@ -284,6 +284,21 @@ def test_triplet_count_brute_force(case):
 
 
 @pytest.mark.parametrize("case", range(len(_HAND) + 6))
+def test_general_storage_triplet_count_brute_force(case):
+    # every (I, J) of the square (both triangles) and K with X~_IK, X~_KJ stored
+    if case < len(_HAND):
+        nb, kept = _HAND[case]
+    else:
+        rng = np.random.default_rng(300 + case)
+        nb = int(rng.integers(2, 9))
+        kept = _random_kept(rng, nb, rng.uniform(0.1, 0.9), drop_diag=set(rng.integers(0, nb, 2).tolist()))
+    stored = set(kept) | {(j, i) for i, j in kept}
+    brute = sum(1 for i in range(nb) for j in range(nb) for k in range(nb)
+                if (i, k) in stored and (k, j) in stored)
+    assert O.triplets_general(kept, nb) == brute
+
+
+@pytest.mark.parametrize("case", range(len(_HAND) + 6))
 def test_product_pattern_matches_nonzero_tiles_of_the_polynomial(case):
     # the tile pattern of X_i = c0 I + c1 X~ + c2 X~^2 (Algorithm 2), found from
     # the arithmetic itself: positive values on the stored tiles and positive
