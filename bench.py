@@ -207,6 +207,8 @@ def main(argv=None) -> int:
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="split16", choices=["fp64", "split16"])
     ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--storage", default="symmetric", choices=["symmetric", "general"],
+                    help="general: both triangles stored and computed (the paper's general-matrix form)")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the timed FP64 reference run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -241,7 +243,7 @@ def main(argv=None) -> int:
 
     def step(F, precision, keep_D=False):
         ctx = sp2.SP2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision=precision,
-                      slices=args.slices)
+                      slices=args.slices, storage=args.storage)
         st = ctx.run()
         D = ctx.D_device() if keep_D else None
         ctx.close()
@@ -317,7 +319,7 @@ def main(argv=None) -> int:
 
         def e2e_step():
             ctx = sp2.SP2(HostF, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"],
-                          precision=args.precision, slices=args.slices)
+                          precision=args.precision, slices=args.slices, storage=args.storage)
             st = ctx.run()
             out = ctx.D_host(Dh)
             ctx.close()
@@ -370,7 +372,7 @@ def main(argv=None) -> int:
         "warmup": args.warmup, "ms_per_step": ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f16x%d-split+f64" % args.slices,
         "data": "synthetic",
-        "config": {"workload": wl["desc"], "precision": args.precision,
+        "config": {"workload": wl["desc"], "precision": args.precision, "storage": args.storage,
                    "slices": args.slices if args.precision == "split16" else None,
                    "l2": "inputs larger than L2 (F alone is %.0f MB)" % (Fh.val.nbytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},

@@ -78,6 +78,12 @@ enum sp2_trunc     { SP2_TRUNC_FROBENIUS = 0, SP2_TRUNC_FROBINF = 1 };
  * Everything else (traces, norms, polynomial choice, stop test, truncation)
  * is FP64 in every precision. */
 enum sp2_precision { SP2_PREC_FP64 = 0, SP2_PREC_SPLIT16 = 1 };
+/* Storage of the iterates (Section 5): SYMMETRIC keeps the upper tiles only and
+ * computes only the upper output tiles of each square; GENERAL keeps and
+ * computes both triangles, like the paper's general-matrix implementation (the
+ * comparison of Section 6).  The truncation selection is the same in both, so
+ * D is the same; D is returned as upper tiles in both. */
+enum sp2_storage   { SP2_STORAGE_SYMMETRIC = 0, SP2_STORAGE_GENERAL = 1 };
 
 typedef struct {
   int64_t n;              /* matrix dimension N                                  */
@@ -134,6 +140,8 @@ typedef struct {
                               tensor-core operand reports an out-of-range element (its data are
                               unchanged) and sp2_run returns SP2_ERR_RANGE.  Later runs of the
                               context are unaffected.                                   */
+  int32_t storage;         /* sp2_storage, default SYMMETRIC; GENERAL does not record masks for
+                              sp2_backward (record_masks must be 0)                    */
 } sp2_params;
 
 typedef struct {
@@ -146,7 +154,8 @@ typedef struct {
   double homo_est, lumo_est; /* Step 3 estimates (NaN when unavailable)                 */
   int32_t have_estimates;  /* bit 0: homo_est valid, bit 1: lumo_est valid */
   int64_t nnzb_final;      /* stored tiles of D                                        */
-  int64_t tile_triplets;   /* sum over squares of (I <= J, K) tile triplets             */
+  int64_t tile_triplets;   /* sum over squares of the (I <= J, K) tile triplets computed
+                              (GENERAL storage: all (I, J, K) of both triangles)        */
   double alg_flops;        /* 2 * 32^3 * tile_triplets                                 */
   double run_ms;           /* device time of sp2_run (cudaEvents)                      */
   double square_ms;        /* device time spent in the tile-product kernels            */

@@ -31,6 +31,7 @@ MODES = {"sp2": 0, "sp2acc": 1, "trace": 2}
 STOPS = {"parameterless": 0, "idempotency": 1}
 TRUNCS = {"frobenius": 0, "frobinf": 1}
 PRECISIONS = {"fp64": 0, "split16": 1}
+STORAGES = {"symmetric": 0, "general": 1}
 
 
 class sp2_bsr(ctypes.Structure):
@@ -47,7 +48,8 @@ class sp2_params(ctypes.Structure):
                 ("frobinf_part", c_int64), ("gamma", c_double), ("delta_acc", c_double), ("n_max_cap", c_int32),
                 ("precision", c_int32), ("slices", c_int32), ("mixed_from", c_int32), ("mixed_until", c_int32),
                 ("ckpt_every", c_int32), ("record_masks", c_int32), ("fp64_tail", c_double),
-                ("acc_flush_min", c_int32), ("wait_limit_ms", c_int32), ("selftest", c_int32)]
+                ("acc_flush_min", c_int32), ("wait_limit_ms", c_int32), ("selftest", c_int32),
+                ("storage", c_int32)]
 
 
 class sp2_stats(ctypes.Structure):
@@ -128,7 +130,7 @@ def sp2_default_params(**overrides) -> sp2_params:
     rc = load().sp2_default_params(byref(p))
     if rc != SP2_OK:
         raise SP2Error(rc, "sp2_default_params")
-    enums = {"mode": MODES, "stop": STOPS, "trunc": TRUNCS, "precision": PRECISIONS}
+    enums = {"mode": MODES, "stop": STOPS, "trunc": TRUNCS, "precision": PRECISIONS, "storage": STORAGES}
     for k, v in overrides.items():
         if k in enums and isinstance(v, str):
             v = enums[k][v]

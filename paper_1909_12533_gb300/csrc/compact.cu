@@ -68,9 +68,9 @@ __global__ void __launch_bounds__(256) k_place(const int32_t* __restrict__ srowp
 }
 
 // Trace of the kept diagonal tiles of a tile set (the trace-correcting choice
-// of Section 1 needs trace(X~) before the next product): rows I whose first
-// tile is (I, I) and kept (keep == nullptr: all kept) add the real part of the
-// tile's diagonal.  One CTA, fixed summation order (deterministic).
+// of Section 1 needs trace(X~) before the next product): rows I whose tile
+// (I, I) is stored and kept (keep == nullptr: all kept) add the real part of
+// the tile's diagonal.  One CTA, fixed summation order (deterministic).
 constexpr int TRACE_T = 1024;
 __global__ void __launch_bounds__(TRACE_T)
     k_trace_kept(const int32_t* __restrict__ rowptr, const int32_t* __restrict__ bcol,
@@ -79,7 +79,13 @@ __global__ void __launch_bounds__(TRACE_T)
   __shared__ double red[TRACE_T];
   double acc = 0.0;
   for (int I = threadIdx.x; I < nb; I += TRACE_T) {
-    const int t = rowptr[I];
+    int lo = rowptr[I], hi = rowptr[I + 1];
+    while (lo < hi) {   // first tile of row I with column >= I
+      const int mid = (lo + hi) >> 1;
+      if (bcol[mid] < I) lo = mid + 1;
+      else hi = mid;
+    }
+    const int t = lo;
     if (t < rowptr[I + 1] && bcol[t] == I && (!keep || keep[t])) {
       const double* x = pool + (int64_t)(slot ? slot[t] : t) * TE;
       for (int r = 0; r < TB && (int64_t)I * TB + r < n; ++r) acc += x[r * (TB + 1)];

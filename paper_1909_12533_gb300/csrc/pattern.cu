@@ -174,15 +174,17 @@ __global__ void k_fill_full(const uint32_t* __restrict__ bits, int nb, int words
 // connects is still an output tile), restricted to J >= I, plus the diagonal.
 __global__ void k_product_bits(const int32_t* __restrict__ arowptr, const int32_t* __restrict__ acol,
                                const uint32_t* __restrict__ abits, const uint32_t* __restrict__ bbits, int nb,
-                               int words, uint32_t* out) {
+                               int words, int upper, uint32_t* out) {
   const int I = blockIdx.x;
   const int a0 = arowptr[I], a1 = arowptr[I + 1];
   for (int w = threadIdx.x; w < words; w += blockDim.x) {
     uint32_t acc = abits[(int64_t)I * words + w];
     for (int e = a0; e < a1; ++e) acc |= bbits[(int64_t)acol[e] * words + w];
     const int lo = w * 32;
-    if (lo + 32 <= I) acc = 0;
-    else if (lo < I) acc &= ~((1u << (I - lo)) - 1u);
+    if (upper) {
+      if (lo + 32 <= I) acc = 0;
+      else if (lo < I) acc &= ~((1u << (I - lo)) - 1u);
+    }
     if ((I >> 5) == w) acc |= 1u << (I & 31);
     out[(int64_t)I * words + w] = acc;
   }
@@ -287,9 +289,9 @@ cudaError_t launch_fill_full(const TileSet& s, int nb, FullPattern& fp, cudaStre
 }
 
 cudaError_t launch_product_bits(const FullPattern& a, const FullPattern& b, int nb, uint32_t* out_bits,
-                                cudaStream_t st) {
+                                cudaStream_t st, bool upper) {
   const int t = a.words >= 128 ? 256 : (a.words >= 32 ? 128 : 32);
-  { ++g_launches; k_product_bits<<<nb, t, 0, st>>>(a.rowptr, a.col, a.bits, b.bits, nb, a.words, out_bits); }
+  { ++g_launches; k_product_bits<<<nb, t, 0, st>>>(a.rowptr, a.col, a.bits, b.bits, nb, a.words, upper ? 1 : 0, out_bits); }
   return cudaGetLastError();
 }
 

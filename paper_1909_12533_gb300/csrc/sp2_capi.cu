@@ -358,6 +358,7 @@ struct sp2_ctx {
   std::vector<Buf> seg;
   Buf ident, fpB_bits, fpB_rowptr, fpB_col, fpB_ref, gpool[2], w_brow, w_bcol, w_rowptr, w_pool, dF;
   Buf amax, trbuf;
+  Buf gflag, gpos, gkeep, u_brow, u_bcol, u_slot;   // general storage: upper sub-index
   FullPattern fpB;
   double backward_ms = 0.0;
   HostBlock* hb = nullptr;
@@ -380,7 +381,8 @@ struct sp2_ctx {
                   &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &opx.sbits,
                   &opx.cnt, &opx.spos, &opx.index, &opx.head, &opx.data, &opy.sbits, &opy.cnt, &opy.spos,
                   &opy.index, &opy.head, &opy.data, &sflag, &spos, &slist, &errflag, &scount, &tcscratch, &redwork, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
-                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax, &trbuf};
+                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax, &trbuf, &gflag, &gpos, &gkeep,
+                  &u_brow, &u_bcol, &u_slot};
     for (Buf* b : all) bufs.push_back(b);
   }
 
@@ -467,14 +469,9 @@ int32_t read_count(sp2_ctx* c, const int32_t* dev) {
 // Truncate the tile set `in` (values indexed by slot, norms in n2[slot]) and
 // compact its index into index set `set`; the kept-tile count is left in dcnt[0]
 // (no host round trip).  Returns the target TileSet (nnzb not yet known).
-TileSet truncate_launch(sp2_ctx* c, const TileSet& in, const double* n2, double tau, int set) {
-  const int64_t part_tiles = std::max<int64_t>(1, c->prm.frobinf_part / TB);
-  // n2 may live in p_n2: only the flag buffers are (re)sized here
-  c->ensure(c->keep, (size_t)std::max<int64_t>(in.nnzb, 1) * 4);
-  c->ensure(c->scanbuf, (size_t)std::max<int64_t>(in.nnzb, 1) * 4);
-  c->ensure(c->twork, trunc_work_bytes(std::max<int64_t>(in.nnzb, 1), c->nb, part_tiles));
-  c->ck(launch_truncate(in, n2, c->nb, tau, c->prm.trunc, part_tiles, c->twork.p, c->keep.as<int32_t>(), c->st),
-        "truncate");
+// Compact the tiles of `in` whose keep flag (c->keep) is set into index set
+// `set`; the kept-tile count is left in dcnt[0] (no host round trip).
+TileSet compact_into_set(sp2_ctx* c, const TileSet& in, int set) {
   const size_t cap = (size_t)std::max<int64_t>(in.nnzb, 1) * 4;
   Buf& br = set ? c->y_brow : c->x_brow;
   Buf& bc = set ? c->y_bcol : c->x_bcol;
@@ -485,6 +482,7 @@ TileSet truncate_launch(sp2_ctx* c, const TileSet& in, const double* n2, double 
   c->ensure(sl, cap);
   c->ensure(rp, (size_t)(c->nb + 1) * 4);
   c->ensure(c->dcnt, 16);
+  c->ensure(c->scanbuf, cap);
   c->ensure(c->scantmp, scan_tmp_bytes(in.nnzb) + 4096);
   TileSet t;
   set_tiles(t, br, bc, sl, rp, 0);
@@ -492,6 +490,53 @@ TileSet truncate_launch(sp2_ctx* c, const TileSet& in, const double* n2, double 
                        c->scanbuf.as<int32_t>(), c->st),
         "compact");
   return t;
+}
+
+// Truncate the tile set `in` (values indexed by slot, norms in n2[slot]) and
+// compact its index into index set `set`; the kept-tile count is left in dcnt[0]
+// (no host round trip).  Returns the target TileSet (nnzb not yet known).
+TileSet truncate_launch(sp2_ctx* c, const TileSet& in, const double* n2, double tau, int set) {
+  const int64_t part_tiles = std::max<int64_t>(1, c->prm.frobinf_part / TB);
+  // n2 may live in p_n2: only the flag buffers are (re)sized here
+  c->ensure(c->keep, (size_t)std::max<int64_t>(in.nnzb, 1) * 4);
+  c->ensure(c->twork, trunc_work_bytes(std::max<int64_t>(in.nnzb, 1), c->nb, part_tiles));
+  c->ck(launch_truncate(in, n2, c->nb, tau, c->prm.trunc, part_tiles, c->twork.p, c->keep.as<int32_t>(), c->st),
+        "truncate");
+  return compact_into_set(c, in, set);
+}
+
+// General storage: the same selection as the symmetric storage, made on the
+// upper tiles of `in` (all of its nb diagonal tiles are present, so there are
+// (nnzb + nb) / 2 of them), then every lower tile follows its mirror.
+TileSet truncate_launch_general(sp2_ctx* c, const TileSet& in, const double* n2, double tau, int set) {
+  const int64_t part_tiles = std::max<int64_t>(1, c->prm.frobinf_part / TB);
+  const int64_t nU = (in.nnzb + c->nb) / 2;
+  const size_t cap = (size_t)std::max<int64_t>(in.nnzb, 1) * 4, capU = (size_t)std::max<int64_t>(nU, 1) * 4;
+  c->ensure(c->gflag, cap);
+  c->ensure(c->gpos, cap);
+  c->ensure(c->gkeep, capU);
+  c->ensure(c->u_brow, capU);
+  c->ensure(c->u_bcol, capU);
+  c->ensure(c->u_slot, capU);
+  c->ensure(c->keep, cap);
+  c->ensure(c->dcnt, 16);
+  c->ensure(c->scantmp, scan_tmp_bytes(in.nnzb) + 4096);
+  c->ensure(c->twork, trunc_work_bytes(std::max<int64_t>(nU, 1), c->nb, part_tiles));
+  c->ck(launch_upper_flags(in, c->gflag.as<int32_t>(), c->st), "upper flags");
+  TileSet U;
+  U.nnzb = nU;
+  U.brow = c->u_brow.as<int32_t>();
+  U.bcol = c->u_bcol.as<int32_t>();
+  U.slot = c->u_slot.as<int32_t>();
+  U.rowptr = nullptr;
+  c->ck(launch_compact(in, c->gflag.as<int32_t>(), c->nb, U, c->dcnt.as<int32_t>() + 1, c->scantmp.p,
+                       c->gpos.as<int32_t>(), c->st),
+        "upper tiles");
+  c->ck(launch_truncate(U, n2, c->nb, tau, c->prm.trunc, part_tiles, c->twork.p, c->gkeep.as<int32_t>(), c->st),
+        "truncate");
+  c->ck(launch_general_keep(in, c->gpos.as<int32_t>(), c->gkeep.as<int32_t>(), c->keep.as<int32_t>(), c->st),
+        "mirror keep");
+  return compact_into_set(c, in, set);
 }
 
 // Make `t` (with its host-side count) the current X~ and build its row offsets.
@@ -519,6 +564,53 @@ void ensure_ident(sp2_ctx* c, int64_t n) {
   if (c->ident.p && c->ident.cap >= (size_t)n * 4) return;
   c->ensure(c->ident, (size_t)std::max<int64_t>(n, 1) * 4);
   c->ck(launch_iota(c->ident.as<int32_t>(), (int64_t)(c->ident.cap / 4), c->st), "iota");
+}
+
+// General storage of X~_0: from the symmetric set c->X (values in pool[cur])
+// to both triangles in index set 1 / pool[1 - cur], slots = tile index.
+void expand_to_general(sp2_ctx* c) {
+  build_full(c, c->X, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
+  const int64_t nG = read_count(c, c->fp.rowptr + c->nb);
+  const size_t cap = (size_t)std::max<int64_t>(nG, 1) * 4;
+  c->ensure(c->y_brow, cap);
+  c->ensure(c->y_bcol, cap);
+  c->ensure(c->y_slot, cap);
+  c->ensure(c->y_rowptr, (size_t)(c->nb + 1) * 4);
+  const int nxt = 1 - c->cur;
+  c->ensure(c->pool[nxt], (size_t)std::max<int64_t>(nG, 1) * TE * 8);
+  c->ck(launch_expand_general(c->fp, c->nb, c->pool[c->cur].as<double>(), c->y_brow.as<int32_t>(),
+                              c->y_bcol.as<int32_t>(), c->pool[nxt].as<double>(), c->st),
+        "expand");
+  c->ck(launch_iota(c->y_slot.as<int32_t>(), nG, c->st), "slots");
+  TileSet g;
+  set_tiles(g, c->y_brow, c->y_bcol, c->y_slot, c->y_rowptr, 0);
+  c->cur = nxt;
+  adopt_X(c, g, nG, 1);
+}
+
+// Row (CSR) and column (CSC) views of the general X~ for the product: A reads
+// row I's tiles (I, K) as stored, B reads column J's tiles (K, J) (REF_T:
+// untransposed).  refs are pool slots (FP64 kernel) or tile indices (tensor
+// path, whose operand records look the slots up).
+void build_general(sp2_ctx* c, bool by_index) {
+  const TileSet& X = c->X;
+  c->ensure(c->fp_bits, (size_t)c->nb * c->words * 4);
+  c->ck(launch_bits_general(X, c->nb, c->words, c->fp_bits.as<uint32_t>(), c->st), "bits");
+  const int32_t* rslot = X.slot;
+  if (by_index) {
+    ensure_ident(c, X.nnzb);
+    rslot = c->ident.as<int32_t>();
+  }
+  c->fp.words = c->words;
+  c->fp.bits = c->fp_bits.as<uint32_t>();
+  c->fp.rowptr = X.rowptr;
+  c->fp.col = X.bcol;
+  c->fp.ref = reinterpret_cast<uint32_t*>(const_cast<int32_t*>(rslot));
+  c->fp.nnz = X.nnzb;
+  c->ensure(c->fpB_ref, (size_t)std::max<int64_t>(X.nnzb, 1) * 4);
+  c->ck(launch_csc_refs(X, by_index ? nullptr : X.slot, c->fpB_ref.as<uint32_t>(), c->st), "csc refs");
+  c->fpB = c->fp;
+  c->fpB.ref = c->fpB_ref.as<uint32_t>();
 }
 
 void record(sp2_ctx* c, int j) {
@@ -627,14 +719,14 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   c->ensure(c->sflag, (size_t)npair * 4);
   c->ensure(c->spos, (size_t)npair * 4);
   c->ensure(c->scantmp, scan_tmp_bytes(npair) + 4096);
-  c->ck(launch_super_flags(obits, c->nb, c->words, nsr, c->sflag.as<int32_t>(), c->st), "super flags");
+  c->ck(launch_super_flags(obits, c->nb, c->words, nsr, c->sflag.as<int32_t>(), c->st, L.general), "super flags");
   c->ensure(c->scount, 16);
   c->ck(launch_scan_i32(c->sflag.as<int32_t>(), c->spos.as<int32_t>(), npair, c->scount.as<int32_t>(),
                         c->scantmp.p, c->st),
         "scan");
   // no host round trip: a persistent kernel with one CTA per SM reads the
   // number of active super-tiles and takes them from a work counter
-  const int64_t ubound = (int64_t)nsr * (nsr + 1) / 2;
+  const int64_t ubound = L.general ? (int64_t)nsr * nsr : (int64_t)nsr * (nsr + 1) / 2;
   c->ensure(c->slist, (size_t)std::max<int64_t>(ubound, 1) * 4);
   c->ck(cudaMemsetAsync(c->scount.as<int32_t>() + 1, 0, 4, c->st), "memset");
   int sms = 0;
@@ -666,10 +758,12 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
 }
 
 // Forward: S = X~^2 on the product pattern (o_bits, upper only) with the fused epilogue.
-void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool) {
+void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool, bool general) {
   TcLaunch L{};
   L.P = prepare_operand(c, c->X, c->pool[c->cur].as<double>(), c->fp, c->opx, 1.0);
-  L.Q = L.P;
+  // general storage: B is read by columns, from its own records
+  L.Q = general ? prepare_operand(c, c->X, c->pool[c->cur].as<double>(), c->fpB, c->opy, 1.0) : L.P;
+  L.general = general;
   L.two_pass = false;
   L.scale = 1.0;
   L.Z = &c->fp;
@@ -726,6 +820,7 @@ int sp2_default_params(sp2_params* p) {
   p->acc_flush_min = 512;
   p->wait_limit_ms = 2000;
   p->selftest = 0;
+  p->storage = SP2_STORAGE_SYMMETRIC;
   return SP2_OK;
 }
 
@@ -806,6 +901,8 @@ int check_create_args(int64_t n, double homo_ub, double lumo_lb, double tau, con
   if (prm.precision == SP2_PREC_SPLIT16 && (prm.slices < 2 || prm.slices > 4)) return SP2_ERR_INVALID_ARG;
   if (prm.ckpt_every < 1) return SP2_ERR_INVALID_ARG;
   if (prm.wait_limit_ms < 1 || prm.selftest < 0 || prm.selftest > 2) return SP2_ERR_INVALID_ARG;
+  if (prm.storage != SP2_STORAGE_SYMMETRIC && prm.storage != SP2_STORAGE_GENERAL) return SP2_ERR_INVALID_ARG;
+  if (prm.storage == SP2_STORAGE_GENERAL && prm.record_masks) return SP2_ERR_INVALID_ARG;
   const int64_t nb64 = (n + TB - 1) / TB;
   if (nb64 > 65535) return SP2_ERR_INVALID_ARG;
   return SP2_OK;
@@ -1039,6 +1136,8 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       adopt_X(c, t0, read_count(c, c->dcnt.as<int32_t>()), 0);
     }
     double tr_cur = trace_mode ? c->h_d2[1] : 0.0;   // trace(X~_{i-1}) in trace mode
+    const bool general = c->prm.storage == SP2_STORAGE_GENERAL;
+    if (general) expand_to_general(c);
     S.nnzb_hist[0] = c->X.nnzb;
     c->tail_from = 0;
     free_recs(c);
@@ -1050,15 +1149,21 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       const bool tc = use_tc(c, i);
       // symbolic: both-triangle pattern of X~_{i-1}, product pattern (upper + diagonal);
       // the tensor path addresses tiles by compact index (slices), the FP64 path by slot
-      TileSet Xc = c->X;
-      if (tc) {
-        ensure_ident(c, c->X.nnzb);
-        Xc.slot = c->ident.as<int32_t>();
+      if (general) {
+        build_general(c, tc);
+      } else {
+        TileSet Xc = c->X;
+        if (tc) {
+          ensure_ident(c, c->X.nnzb);
+          Xc.slot = c->ident.as<int32_t>();
+        }
+        build_full(c, Xc, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
       }
-      build_full(c, Xc, c->fp, c->fp_bits, c->fp_rowptr, c->fp_col, c->fp_ref);
       c->ensure(c->o_bits, (size_t)c->nb * c->words * 4);
       c->ensure(c->o_rowptr, (size_t)(c->nb + 1) * 4);
-      c->ck(launch_product_bits(c->fp, c->fp, c->nb, c->o_bits.as<uint32_t>(), c->st), "product bits");
+      c->ensure(c->counts, (size_t)(c->nb + 1) * 4);
+      c->ensure(c->scantmp, scan_tmp_bytes(c->nb + 1) + 4096);
+      c->ck(launch_product_bits(c->fp, c->fp, c->nb, c->o_bits.as<uint32_t>(), c->st, !general), "product bits");
       c->ck(launch_row_popc(c->o_bits.as<uint32_t>(), c->nb, c->words, c->counts.as<int32_t>(), c->st), "popc");
       c->ck(launch_scan_i32(c->counts.as<int32_t>(), c->o_rowptr.as<int32_t>(), c->nb,
                             c->o_rowptr.as<int32_t>() + c->nb, c->scantmp.p, c->st),
@@ -1089,15 +1194,16 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       coeffs(p, a, c0, c1, c2);
       SquareArgs sa;
       sa.A = &c->fp; sa.apool = c->pool[c->cur].as<double>();
-      sa.B = &c->fp; sa.bpool = sa.apool;
+      sa.B = general ? &c->fpB : &c->fp; sa.bpool = sa.apool;
       sa.sym_sum = false;
+      sa.general = general;
       sa.Z = &c->fp; sa.zpool = sa.apool;
       sa.out = &c->out; sa.outpool = c->pool[nxt].as<double>();
       sa.c0 = c0; sa.c1 = c1; sa.c2 = c2;
       sa.n = c->n; sa.nb = c->nb;
       sa.part = partials(c);
       if (tc) {
-        square_tc(c, c0, c1, c2, sa.outpool);
+        square_tc(c, c0, c1, c2, sa.outpool, general);
       } else {
         c->ck(cudaEventRecord(c->evs0, c->st), "event");
         c->ck(launch_square_f64(sa, c->st), "square f64");
@@ -1110,7 +1216,9 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       // live in pool[nxt] at slot = output index); X~_{i-1} keeps its own index set
       const bool more = i <= sch.n_max;
       TileSet next;
-      if (more) next = truncate_launch(c, c->out, c->p_n2.as<double>(), sch.tau[i], 1 - c->xset);
+      if (more)
+        next = general ? truncate_launch_general(c, c->out, c->p_n2.as<double>(), sch.tau[i], 1 - c->xset)
+                       : truncate_launch(c, c->out, c->p_n2.as<double>(), sch.tau[i], 1 - c->xset);
       if (more && trace_mode) {
         // trace(X~_i) for the next choice: the kept diagonal tiles of the output
         c->ck(launch_trace_kept(c->out, c->keep.as<int32_t>(), c->pool[nxt].as<double>(), c->nb, c->n,
@@ -1177,13 +1285,31 @@ int sp2_run(sp2_ctx* c, sp2_stats* stats_out) {
       S.nnzb_hist[i] = c->X.nnzb;
       record(c, i);
     }
-    // D = X~_n: contiguous copy for the caller's view
-    c->d_nnzb = c->X.nnzb;
+    // D = X~_n: contiguous copy of its upper tiles for the caller's view
+    TileSet Dx = c->X;
+    if (general) {
+      c->ensure(c->gflag, (size_t)std::max<int64_t>(c->X.nnzb, 1) * 4);
+      c->ensure(c->gpos, (size_t)std::max<int64_t>(c->X.nnzb, 1) * 4);
+      c->ensure(c->u_brow, (size_t)std::max<int64_t>(c->X.nnzb, 1) * 4);
+      c->ensure(c->u_bcol, (size_t)std::max<int64_t>(c->X.nnzb, 1) * 4);
+      c->ensure(c->u_slot, (size_t)std::max<int64_t>(c->X.nnzb, 1) * 4);
+      c->ensure(c->scantmp, scan_tmp_bytes(c->X.nnzb) + 4096);
+      c->ck(launch_upper_flags(c->X, c->gflag.as<int32_t>(), c->st), "upper flags");
+      Dx.brow = c->u_brow.as<int32_t>();
+      Dx.bcol = c->u_bcol.as<int32_t>();
+      Dx.slot = c->u_slot.as<int32_t>();
+      Dx.rowptr = nullptr;
+      c->ck(launch_compact(c->X, c->gflag.as<int32_t>(), c->nb, Dx, c->dcnt.as<int32_t>(), c->scantmp.p,
+                           c->gpos.as<int32_t>(), c->st),
+            "upper tiles");
+      Dx.nnzb = read_count(c, c->dcnt.as<int32_t>());
+    }
+    c->d_nnzb = Dx.nnzb;
     c->ensure(c->d_brow, std::max<int64_t>(c->d_nnzb, 1) * 4);
     c->ensure(c->d_bcol, std::max<int64_t>(c->d_nnzb, 1) * 4);
     c->ensure(c->d_val, (size_t)std::max<int64_t>(c->d_nnzb, 1) * TE * 8);
-    c->ck(launch_copy_index(c->X, c->d_brow.as<int32_t>(), c->d_bcol.as<int32_t>(), c->st), "copy index");
-    c->ck(launch_gather_tiles(c->X, c->pool[c->cur].as<double>(), c->d_val.as<double>(), c->st), "gather");
+    c->ck(launch_copy_index(Dx, c->d_brow.as<int32_t>(), c->d_bcol.as<int32_t>(), c->st), "copy index");
+    c->ck(launch_gather_tiles(Dx, c->pool[c->cur].as<double>(), c->d_val.as<double>(), c->st), "gather");
     c->ck(cudaEventRecord(c->ev1, c->st), "event");
     c->sync();
     float ms = 0.f;

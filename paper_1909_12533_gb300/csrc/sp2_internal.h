@@ -64,8 +64,10 @@ cudaError_t launch_scan_i32(const int32_t* in, int32_t* out_excl, int64_t n, int
                             void* tmp, cudaStream_t st);
 size_t scan_tmp_bytes(int64_t n);
 cudaError_t launch_fill_full(const TileSet& s, int nb, FullPattern& fp, cudaStream_t st);
+// out row I = a's row I | OR over K in a's row I of b's row K | {I}; upper:
+// only J >= I (symmetric storage), else the whole row (general storage)
 cudaError_t launch_product_bits(const FullPattern& a, const FullPattern& b, int nb, uint32_t* out_bits,
-                                cudaStream_t st);
+                                cudaStream_t st, bool upper = true);
 cudaError_t launch_fill_upper_from_bits(const uint32_t* bits, int nb, int words, const int32_t* rowptr,
                                         int32_t* brow, int32_t* bcol, int32_t* slot, cudaStream_t st);
 cudaError_t launch_rowptr_from_brow(const int32_t* brow, int64_t nnzb, int nb, int32_t* rowptr,
@@ -90,6 +92,7 @@ struct SquareArgs {
   double c0, c1, c2;
   int64_t n; int nb;
   Partials part;
+  bool general = false;                         // both triangles stored: every tile has weight 1 in e^2
 };
 cudaError_t launch_square_f64(const SquareArgs& a, cudaStream_t st);
 size_t reduce_work_bytes();
@@ -126,6 +129,17 @@ cudaError_t launch_dense_tile_fill(const double* F, int64_t n, int64_t ld, int n
 cudaError_t launch_tiles_to_dense(const int32_t* brow, const int32_t* bcol, const double* val, int64_t nnzb,
                                   int64_t n, int64_t ld, double* out, cudaStream_t st);
 
+// general.cu: general (both-triangle) storage of the iterates
+cudaError_t launch_bits_general(const TileSet& s, int nb, int words, uint32_t* bits, cudaStream_t st);
+// CSC view of a general set with a symmetric pattern: ref[t] = slot (or index) of the mirror of t | REF_T
+cudaError_t launch_csc_refs(const TileSet& s, const int32_t* slot, uint32_t* ref, cudaStream_t st);
+// general set (entries of fp, values transposed where ref has REF_T) from a symmetric set's pool
+cudaError_t launch_expand_general(const FullPattern& fp, int nb, const double* src, int32_t* brow, int32_t* bcol,
+                                  double* dst, cudaStream_t st);
+cudaError_t launch_upper_flags(const TileSet& s, int32_t* flag, cudaStream_t st);
+cudaError_t launch_general_keep(const TileSet& s, const int32_t* posU, const int32_t* keepU, int32_t* keep,
+                                cudaStream_t st);
+
 // square_tc.cu: tcgen05 FP16-slice product (see the file header).  An
 // operand is stored as panel records: for each super-row R (tile rows
 // 4R..4R+3) and K tile present in its super-row bitmap, a header byte and the
@@ -160,6 +174,7 @@ struct TcLaunch {
   int seg_min;               // K loops of at least this many steps are accumulated in 16-step segments (0: never)
   unsigned long long wait_ns = 2000000000ull;   // limit of every bounded wait in the kernel
   bool selftest = false;     // wait first on a barrier nothing arrives at (tests the timeout path)
+  bool general = false;      // general storage: every output tile of the square, weight 1 in e^2
 };
 size_t panel_record_bytes(int k);
 // report_range: also report an out-of-range element (error bit 4) without one
@@ -174,7 +189,8 @@ cudaError_t launch_absmax(const TileSet& x, const double* pool, unsigned long lo
 cudaError_t launch_upper_bits(const TileSet& x, int nb, int words, uint32_t* bits, cudaStream_t st);
 cudaError_t launch_super_bits(const FullPattern& fp, int nb, int nsr, uint32_t* sb, cudaStream_t st);
 int64_t super_order_size(int nsr);   // length of the (padded) launch-order index space
-cudaError_t launch_super_flags(const uint32_t* obits, int nb, int words, int nsr, int32_t* flag, cudaStream_t st);
+cudaError_t launch_super_flags(const uint32_t* obits, int nb, int words, int nsr, int32_t* flag, cudaStream_t st,
+                               bool general = false);
 cudaError_t launch_super_fill(const int32_t* flag, const int32_t* pos, int64_t n, int nsr, int32_t* list,
                               cudaStream_t st);
 cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st);

@@ -39,6 +39,7 @@ struct SqDev {
   double c0, c1, c2;
   int64_t n;
   int words;
+  int general;   // both triangles stored: no mirror weight
   Partials part;
 };
 
@@ -149,7 +150,7 @@ __global__ void __launch_bounds__(256) k_square_f64(SqDev a) {
       if (dg) { trS += s; trX += z; }
     }
   }
-  const double w = (I == J) ? 1.0 : 2.0;
+  const double w = (I == J || a.general) ? 1.0 : 2.0;
   e2 = block_sum(e2, red);
   if (threadIdx.x == 0) a.part.e2[t] = w * e2;
   n2 = block_sum(n2, red);
@@ -234,6 +235,7 @@ cudaError_t launch_square_f64(const SquareArgs& a, cudaStream_t st) {
   d.obrow = a.out->brow; d.obcol = a.out->bcol; d.oslot = a.out->slot; d.opool = a.outpool;
   d.c0 = a.c0; d.c1 = a.c1; d.c2 = a.c2;
   d.n = a.n; d.words = a.A->words;
+  d.general = a.general ? 1 : 0;
   d.part = a.part;
   if (a.sym_sum) { ++g_launches; k_square_f64<true><<<(unsigned)a.out->nnzb, 256, 0, st>>>(d); }
   else { ++g_launches; k_square_f64<false><<<(unsigned)a.out->nnzb, 256, 0, st>>>(d); }

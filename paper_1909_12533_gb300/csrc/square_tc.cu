@@ -339,14 +339,16 @@ __device__ inline void blocked_decode(int64_t i, int nsr, int& R, int& C) {
   C = (int)((b % nbc) * CB + w % CB);
 }
 
-// flag of the i-th super-tile (R, C) in launch order: R <= C and an output tile present
-__global__ void k_super_flags(const uint32_t* __restrict__ obits, int nb, int words, int nsr, int32_t* flag) {
+// flag of the i-th super-tile (R, C) in launch order: an output tile present
+// (and R <= C unless the storage is general)
+__global__ void k_super_flags(const uint32_t* __restrict__ obits, int nb, int words, int nsr, int general,
+                              int32_t* flag) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= blocked_size(nsr)) return;
   int R, C;
   blocked_decode(i, nsr, R, C);
   int f = 0;
-  if (R < nsr && C < nsr && R <= C) {
+  if (R < nsr && C < nsr && (general || R <= C)) {
     for (int a = 0; a < 4 && !f; ++a) {
       const int row = 4 * R + a;
       if (row >= nb) break;
@@ -403,6 +405,7 @@ struct TcArgs {
   int seg_min;              // K loops of at least this many steps are cut into 16-step segments (0: never)
   unsigned long long wait_ns;   // limit of every bounded wait
   int selftest;             // 1: the producer first waits on a barrier nothing arrives at (timeout path test)
+  int general;              // general storage: output tiles on both sides of the diagonal, weight 1 in e^2
 };
 
 // A pipeline stage holds one sub-step: two A units and two B units, a unit
@@ -880,7 +883,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int Jb = J0 + bt0 + h;
-        oidx[h] = (Ia < a.nb && Jb < a.nb && Ia <= Jb) ? find(a.obits, a.orowptr, Ia, Jb) : -1;
+        oidx[h] = (Ia < a.nb && Jb < a.nb && (a.general || Ia <= Jb)) ? find(a.obits, a.orowptr, Ia, Jb) : -1;
       }
       // phase 1, once per accumulation segment: TMEM -> the exact fixed-point
       // sums of this thread's row in the scratch (the first segment stores, the
@@ -1012,7 +1015,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
         }
         if (lane == 0) {
           const bool diag = Ia == Jb;
-          a.part.e2[oi] = (diag ? 1.0 : 2.0) * e2;
+          a.part.e2[oi] = (diag || a.general ? 1.0 : 2.0) * e2;
           a.part.n2[oi] = n2;
           a.part.trS[oi] = diag ? trS : 0.0;
           a.part.trX[oi] = diag ? trX : 0.0;
@@ -1139,9 +1142,10 @@ cudaError_t launch_super_bits(const FullPattern& fp, int nb, int nsr, uint32_t* 
 
 int64_t super_order_size(int nsr) { return blocked_size(nsr); }
 
-cudaError_t launch_super_flags(const uint32_t* obits, int nb, int words, int nsr, int32_t* flag, cudaStream_t st) {
+cudaError_t launch_super_flags(const uint32_t* obits, int nb, int words, int nsr, int32_t* flag, cudaStream_t st,
+                               bool general) {
   ++g_launches;
-  k_super_flags<<<grid_for(blocked_size(nsr), 256), 256, 0, st>>>(obits, nb, words, nsr, flag);
+  k_super_flags<<<grid_for(blocked_size(nsr), 256), 256, 0, st>>>(obits, nb, words, nsr, general ? 1 : 0, flag);
   return cudaGetLastError();
 }
 
@@ -1166,6 +1170,7 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   a.seg_min = L.seg_min;
   a.wait_ns = L.wait_ns;
   a.selftest = L.selftest ? 1 : 0;
+  a.general = L.general ? 1 : 0;
   cudaError_t e = cudaSuccess;
   switch (L.k) {
     case 2:

@@ -40,10 +40,9 @@ def test_split16_first_square_matches_fp64_closely():
     a = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], n_max_cap=1)
     b = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], n_max_cap=1, precision="split16", slices=4)
     ea, eb = a["stats"]["e"], b["stats"]["e"]
-    # e_0, t_0: one tensor-core square from the same X~_0
-    np.testing.assert_allclose(eb[0], ea[0], rtol=1e-12, atol=1e-9)
-    np.testing.assert_allclose(b["stats"]["t"][0], a["stats"]["t"][0], rtol=1e-12, atol=1e-9)
-    # e_1, t_1 also carry the first square's rounding in X~_1 (measured 1.2e-10 relative)
+    # each element of S carries the slicing of ~1000 products (~1e-12), so
+    # |e_a - e_b| <= ||S_a - S_b||_F ~ 1e-9 on 5.9M elements (measured 1.4e-9 on
+    # e_0 = 11.9, 1.2e-10 relative)
     np.testing.assert_allclose(eb, ea, rtol=1e-9)
     np.testing.assert_allclose(b["stats"]["t"], a["stats"]["t"], rtol=1e-9)
     # 5.9M elements, each within ~1e-12 (2^-44 grid, FP32-exact groups)
