@@ -16,8 +16,9 @@ What each function follows:
                               uncited companion paper, so they are a stated reading
                               (see ``schedule``); tau_i in gamma mode is Eq. (7)
   truncate_* ................ Section 2 (X~_i = X_i + E_i, ||E_i|| <= tau_i, Eqs. (6)-(8))
-                              and Section 3 (Frob-Inf norm, Eq. (13)); selection
-                              rule is a stated reading
+                              and Section 3 (Frob-Inf norm, Eq. (13); the
+                              Frobenius-spectral mixed norm); selection rules are
+                              stated readings
   sp2 ....................... Algorithms 1 and 2
   triplets_general .......... Section 5 (general storage: both triangles computed)
   homo_lumo_estimates ....... Section 4 Step 3 (reading; see the function)
@@ -244,6 +245,74 @@ def _prefix_cut(norm2: np.ndarray, weight: np.ndarray, lin: np.ndarray, budget: 
     return drop
 
 
+MIXED_POWER_ITERS = 100     # power iterations of the mixed-norm bound (reading, see mixed_norm_bound)
+MIXED_MAX_BLOCKS = 512      # largest partition count of the mixed norm
+
+
+def mixed_norm_bound(B2: np.ndarray) -> float:
+    """Upper bound of the spectral norm of the block-norm matrix M = sqrt(B2)
+    (B2: symmetric, nonnegative, the squared Frobenius norms of the blocks of a
+    symmetric E), i.e. of the Frobenius-spectral mixed norm ||E||_m of Section
+    3.  M >= 0, so ||M||_2 = rho(M), and for every positive x the
+    Collatz-Wielandt bound rho(M) <= max_i (M x)_i / x_i holds (rows that are
+    all zero are isolated and skipped).  Reading: x starts at all ones; each of
+    MIXED_POWER_ITERS steps takes the bound u = max_i (M x)_i / x_i, then moves x
+    to (M x + u x) / max(M x + u x) -- a power step on M + u I, which keeps x
+    positive and converges inside every connected block of M also when M has
+    eigenvalues -rho; the smallest bound is returned.  Row sums are sequential
+    (the order the library uses)."""
+    M = np.sqrt(B2.astype(np.float64))
+    live = M.max(axis=1) > 0.0
+    if not np.any(live):
+        return 0.0
+    M = M[np.ix_(live, live)]
+    x = np.ones(M.shape[0])
+    best = math.inf
+    for _ in range(MIXED_POWER_ITERS):
+        y = np.cumsum(M * x[None, :], axis=1)[:, -1]
+        u = float(np.max(y / x))
+        best = min(best, u)
+        z = y + u * x
+        x = z / float(np.max(z))
+    return best
+
+
+def _mixed_cut(n2, weight, R, C, nsb, tau):
+    """Reading of 'truncate so that ||E||_m <= tau' (Section 3): drop every
+    candidate tile whose squared norm is at most a threshold theta, for the
+    largest theta (found by bisection over the 63-bit patterns of the squared
+    norms, which order like the values) whose error matrix has a mixed-norm
+    bound (mixed_norm_bound) of at most tau.  Block sums are exact integers in
+    units of tau^2 2^-36 with each tile's share rounded up (as in _prefix_cut),
+    so the bound never understates ||E||_m.  Returns the boolean 'drop' mask."""
+    drop = np.zeros(n2.shape[0], dtype=bool)
+    if n2.shape[0] == 0:
+        return drop
+    if tau == 0.0:
+        return n2 == 0.0
+    s = Q_SCALE / (tau * tau)
+    q = np.minimum(np.ceil(weight * n2 * s), Q_CAP).astype(np.int64)
+    bits = n2.view(np.int64)
+    limit = 2.0 ** 18          # tau in units of tau 2^-18 (the square root of the unit)
+
+    def bound(theta):
+        sel = bits <= theta
+        B2 = np.zeros((nsb, nsb), dtype=np.int64)
+        np.add.at(B2, (R[sel], C[sel]), q[sel])
+        off = sel & (R != C)
+        np.add.at(B2, (C[off], R[off]), q[off])
+        return mixed_norm_bound(B2)
+
+    lo, hi = 0, 2 ** 63 - 1
+    while hi - lo > 1:
+        mid = lo + (hi - lo) // 2
+        if bound(mid) <= limit:
+            lo = mid
+        else:
+            hi = mid
+    return bits <= lo
+
+
 def truncate_select(X: np.ndarray, tau: float, mode: str = "frobenius", part: int = FROBINF_PART,
                     pattern: set | None = None, b: int = B):
     """Choose the upper tiles to drop from X so that ||E||_F <= tau ("frobenius")
@@ -286,6 +355,17 @@ def truncate_select(X: np.ndarray, tau: float, mode: str = "frobenius", part: in
                 else:
                     w = np.ones(sel.size)
                 drop[sel] = _prefix_cut(n2[sel], w, lin[sel], beta * beta)
+    elif mode == "mixed":
+        # Frobenius-spectral mixed norm of Section 3 on the partition of `part`
+        # rows; weight 2 for an off-diagonal tile inside a diagonal block (its
+        # mirror lies in the same block)
+        pt = part // b
+        R, Cc = ii // pt, jj // pt
+        nsb = (nb + pt - 1) // pt
+        if nsb > MIXED_MAX_BLOCKS:
+            raise ValueError("too many blocks for the mixed norm")
+        w = np.where((R == Cc) & (ii != jj), 2.0, 1.0)
+        drop = _mixed_cut(n2, w, R, Cc, nsb, float(tau))
     else:
         raise ValueError(mode)
     kept = [(int(a), int(c)) for a, c, d in zip(ii, jj, drop) if not d]

@@ -530,3 +530,66 @@ def test_two_run_bounds_bracket_the_gap(key):
         assert np.linalg.norm(r2.D - O.eig_projector(F, c["nocc"])) < 1e-12
     with pytest.raises(ValueError):
         O.bounds_from_estimates(None, 0.5, -1.0, 1.0)
+
+
+# ----------------------------------------------------------------- mixed-norm truncation (Section 3)
+def _exact_mixed(E, part):
+    n = E.shape[0]
+    e = np.append(np.arange(0, n, part), n)
+    k = len(e) - 1
+    Bm = np.array([[np.linalg.norm(E[e[i]:e[i + 1], e[j]:e[j + 1]]) for j in range(k)] for i in range(k)])
+    return float(np.abs(np.linalg.eigvalsh(Bm)).max())
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_mixed_norm_bound_is_an_upper_bound_close_to_rho(seed):
+    # Collatz-Wielandt: the bound is >= the Perron root of M = sqrt(B2), and the
+    # power steps bring it close to it
+    rng = np.random.default_rng(seed)
+    k = int(rng.integers(1, 40))
+    B = rng.uniform(0.0, 1.0, (k, k)) * (rng.random((k, k)) < 0.5)
+    B2 = np.round((B + B.T) ** 2 * 2 ** 20)
+    rho = float(np.abs(np.linalg.eigvalsh(np.sqrt(B2))).max())
+    ub = O.mixed_norm_bound(B2.astype(np.int64))
+    assert ub >= rho * (1 - 1e-12)
+    assert ub <= rho * (1 + 1e-6) + 1e-12
+
+
+@pytest.mark.parametrize("tau,part", [(1e-4, 128), (1e-2, 128), (1e-1, 256), (1.0, 96)])
+def test_mixed_truncation_norm_chain_and_near_maximal(tau, part):
+    # Section 3: ||E||_2 <= ||E||_m <= tau for the dropped E; dropping the next
+    # candidate too would pass tau (the bound is within 1e-6 of ||.||_m)
+    rng = np.random.default_rng(17)
+    n = 800
+    A = _sym(rng, n)
+    d = np.abs(np.subtract.outer(np.arange(n), np.arange(n)))
+    A *= np.exp(-d / 40.0)
+    _, kept, dropped = O.truncate_select(A, tau, "mixed", part=part)
+    E = A - O.apply_drop(A, dropped)
+    m = _exact_mixed(E, part)
+    assert np.linalg.norm(E, 2) <= m * (1 + 1e-12) and m <= tau * (1 + 1e-12)
+    assert len(dropped) > 0
+    _, tiles = O.upper_tiles(A)
+    n2 = {(i, j): v for i, j, v in tiles}
+    nxt = min(kept, key=lambda t: n2[t])
+    E2 = A - O.apply_drop(A, dropped + [nxt])
+    assert _exact_mixed(E2, part) > tau * (1 - 1e-5)
+
+
+def test_mixed_truncation_with_one_block_is_the_frobenius_rule():
+    # one block: ||E||_m = ||E||_F, and the threshold on the squared norms drops
+    # the same tiles as the Frobenius prefix rule (no equal norms here)
+    rng = np.random.default_rng(5)
+    n = 4 * 32 - 7
+    X = _sym(rng, n)
+    e = O.tile_grid(n)
+    for i in range(4):
+        for j in range(i, 4):
+            sc = 10.0 ** rng.uniform(-6, -2)
+            X[e[i]:e[i + 1], e[j]:e[j + 1]] *= sc
+            X[e[j]:e[j + 1], e[i]:e[i + 1]] = X[e[i]:e[i + 1], e[j]:e[j + 1]].T
+    for tau in (1e-6, 1e-4, 1e-3, 1e-2):
+        a = O.truncate_select(X, tau, "mixed", part=4096)
+        b = O.truncate_select(X, tau, "frobenius")
+        assert a[1] == b[1]
+    assert O.truncate_select(X, 0.0, "mixed", part=64)[2] == []
