@@ -66,8 +66,14 @@ extern "C" {
 enum sp2_mode      { SP2_MODE_SP2 = 0, SP2_MODE_SP2ACC = 1, SP2_MODE_TRACE = 2 };
 /* Stop tests: Algorithm 2's parameterless criterion, or e_j < idem_tol. */
 enum sp2_stop      { SP2_STOP_PARAMETERLESS = 0, SP2_STOP_IDEMPOTENCY = 1 };
-/* Truncation norm: Frobenius (Section 2) or Frob-Inf (Section 3, Eq. (13)). */
-enum sp2_trunc     { SP2_TRUNC_FROBENIUS = 0, SP2_TRUNC_FROBINF = 1 };
+/* Truncation norm: Frobenius (Section 2), Frob-Inf (Section 3, Eq. (13)) or the
+ * Frobenius-spectral mixed norm ||.||_m of Section 3 (the spectral norm of the
+ * matrix of block Frobenius norms; blocks of frobinf_part rows, at most 512
+ * block rows).  MIXED: every tile whose squared norm is at most a threshold is
+ * dropped, for the largest threshold whose error has a mixed-norm bound (a
+ * Collatz-Wielandt bound from 100 power steps) of at most tau; found by
+ * bisection with one host round trip per step. */
+enum sp2_trunc     { SP2_TRUNC_FROBENIUS = 0, SP2_TRUNC_FROBINF = 1, SP2_TRUNC_MIXED = 2 };
 /* Arithmetic of the tile products X~ X~:
  *   FP64   : FP64 fused multiply-adds on the CUDA cores.
  *   SPLIT16: tcgen05 tensor-core MMAs on FP16 slices of X~ on fixed absolute
@@ -111,7 +117,8 @@ typedef struct {
   int32_t stop;            /* sp2_stop, default PARAMETERLESS                           */
   double idem_tol;         /* threshold of the idempotency stop, default 1e-12          */
   int32_t trunc;           /* sp2_trunc, default FROBENIUS                              */
-  int64_t frobinf_part;    /* Frob-Inf partition size in rows, multiple of 32; default 4096 (Section 6) */
+  int64_t frobinf_part;    /* Frob-Inf and mixed-norm partition size in rows, multiple of 32;
+                              default 4096 (Section 6)                                  */
   double gamma;            /* > 0: tau_i from Eq. (7) with this gamma; tau argument ignored */
   double delta_acc;        /* acceleration switches off once max distance <= delta_acc; default 0.1 */
   int32_t n_max_cap;       /* cap on n_max, <= SP2_MAX_ITER - 2; default 100             */
@@ -256,8 +263,9 @@ int sp2_backward(sp2_ctx* ctx, const sp2_bsr* W, sp2_bsr* dF_view);
  * tau / max(m_R, m_C) in FROBINF mode (frobinf_part rows, multiple of 32).
  * Budget sums are exact integers in units of budget * 2^-36 (shares rounded
  * up).  keep[nnzb] (same residency as X) receives 1 = kept, 0 = dropped.
- * Allocates its scratch with cudaMallocAsync on cuda_stream and synchronises
- * that stream before returning.  Errors: INVALID_ARG, OOM, CUDA. */
+ * MIXED mode (the mixed norm of Section 3) uses the threshold rule described
+ * at sp2_trunc.  Allocates its scratch with cudaMallocAsync on cuda_stream and
+ * synchronises that stream before returning.  Errors: INVALID_ARG, OOM, CUDA. */
 int sp2_truncate(const sp2_bsr* X, double tau, int32_t mode, int64_t frobinf_part, int32_t* keep,
                  void* cuda_stream);
 
@@ -282,7 +290,8 @@ int sp2_truncate(const sp2_bsr* X, double tau, int32_t mode, int64_t frobinf_par
  * previous call's contents; everything that must start at zero is cleared
  * inside the call.  Calls on the same device that overlap on the GPU (for
  * example queued on two streams) race on that device's array: serialise them.
- * No cudaMalloc, cudaFree or other allocating routine is called.
+ * No cudaMalloc, cudaFree or other allocating routine is called.  Modes
+ * FROBENIUS and FROBINF only (MIXED returns SP2_ERR_INVALID_ARG).
  * Errors: INVALID_ARG, TOO_LARGE, CUDA. */
 int sp2_truncate_noalloc(const int32_t* brow, const int32_t* bcol, const double* val, int64_t n, int64_t nnzb,
                          double tau, int32_t mode, int64_t frobinf_part, int32_t* keep, void* cuda_stream);

@@ -29,7 +29,7 @@ ERRORS = {
 NOT_CONVERGED = -7
 MODES = {"sp2": 0, "sp2acc": 1, "trace": 2}
 STOPS = {"parameterless": 0, "idempotency": 1}
-TRUNCS = {"frobenius": 0, "frobinf": 1}
+TRUNCS = {"frobenius": 0, "frobinf": 1, "mixed": 2}
 PRECISIONS = {"fp64": 0, "split16": 1}
 STORAGES = {"symmetric": 0, "general": 1}
 

@@ -469,6 +469,19 @@ int32_t read_count(sp2_ctx* c, const int32_t* dev) {
 // Truncate the tile set `in` (values indexed by slot, norms in n2[slot]) and
 // compact its index into index set `set`; the kept-tile count is left in dcnt[0]
 // (no host round trip).  Returns the target TileSet (nnzb not yet known).
+// keep flags of the tiles of `in` under the context's truncation norm
+void select_keep(sp2_ctx* c, const TileSet& in, const double* n2, double tau, int32_t* keep) {
+  const int64_t part_tiles = std::max<int64_t>(1, c->prm.frobinf_part / TB);
+  const int64_t nsb = (c->nb + part_tiles - 1) / part_tiles;
+  if (c->prm.trunc == SP2_TRUNC_MIXED) {
+    c->ensure(c->twork, mixed_work_bytes(std::max<int64_t>(in.nnzb, 1), (int)nsb));
+    c->ck(mixed_select(in, n2, c->nb, tau, part_tiles, c->twork.p, keep, c->st), "mixed-norm truncation");
+    return;
+  }
+  c->ensure(c->twork, trunc_work_bytes(std::max<int64_t>(in.nnzb, 1), c->nb, part_tiles));
+  c->ck(launch_truncate(in, n2, c->nb, tau, c->prm.trunc, part_tiles, c->twork.p, keep, c->st), "truncate");
+}
+
 // Compact the tiles of `in` whose keep flag (c->keep) is set into index set
 // `set`; the kept-tile count is left in dcnt[0] (no host round trip).
 TileSet compact_into_set(sp2_ctx* c, const TileSet& in, int set) {
@@ -496,12 +509,9 @@ TileSet compact_into_set(sp2_ctx* c, const TileSet& in, int set) {
 // compact its index into index set `set`; the kept-tile count is left in dcnt[0]
 // (no host round trip).  Returns the target TileSet (nnzb not yet known).
 TileSet truncate_launch(sp2_ctx* c, const TileSet& in, const double* n2, double tau, int set) {
-  const int64_t part_tiles = std::max<int64_t>(1, c->prm.frobinf_part / TB);
   // n2 may live in p_n2: only the flag buffers are (re)sized here
   c->ensure(c->keep, (size_t)std::max<int64_t>(in.nnzb, 1) * 4);
-  c->ensure(c->twork, trunc_work_bytes(std::max<int64_t>(in.nnzb, 1), c->nb, part_tiles));
-  c->ck(launch_truncate(in, n2, c->nb, tau, c->prm.trunc, part_tiles, c->twork.p, c->keep.as<int32_t>(), c->st),
-        "truncate");
+  select_keep(c, in, n2, tau, c->keep.as<int32_t>());
   return compact_into_set(c, in, set);
 }
 
@@ -509,7 +519,6 @@ TileSet truncate_launch(sp2_ctx* c, const TileSet& in, const double* n2, double 
 // upper tiles of `in` (all of its nb diagonal tiles are present, so there are
 // (nnzb + nb) / 2 of them), then every lower tile follows its mirror.
 TileSet truncate_launch_general(sp2_ctx* c, const TileSet& in, const double* n2, double tau, int set) {
-  const int64_t part_tiles = std::max<int64_t>(1, c->prm.frobinf_part / TB);
   const int64_t nU = (in.nnzb + c->nb) / 2;
   const size_t cap = (size_t)std::max<int64_t>(in.nnzb, 1) * 4, capU = (size_t)std::max<int64_t>(nU, 1) * 4;
   c->ensure(c->gflag, cap);
@@ -521,7 +530,6 @@ TileSet truncate_launch_general(sp2_ctx* c, const TileSet& in, const double* n2,
   c->ensure(c->keep, cap);
   c->ensure(c->dcnt, 16);
   c->ensure(c->scantmp, scan_tmp_bytes(in.nnzb) + 4096);
-  c->ensure(c->twork, trunc_work_bytes(std::max<int64_t>(nU, 1), c->nb, part_tiles));
   c->ck(launch_upper_flags(in, c->gflag.as<int32_t>(), c->st), "upper flags");
   TileSet U;
   U.nnzb = nU;
@@ -532,8 +540,7 @@ TileSet truncate_launch_general(sp2_ctx* c, const TileSet& in, const double* n2,
   c->ck(launch_compact(in, c->gflag.as<int32_t>(), c->nb, U, c->dcnt.as<int32_t>() + 1, c->scantmp.p,
                        c->gpos.as<int32_t>(), c->st),
         "upper tiles");
-  c->ck(launch_truncate(U, n2, c->nb, tau, c->prm.trunc, part_tiles, c->twork.p, c->gkeep.as<int32_t>(), c->st),
-        "truncate");
+  select_keep(c, U, n2, tau, c->gkeep.as<int32_t>());
   c->ck(launch_general_keep(in, c->gpos.as<int32_t>(), c->gkeep.as<int32_t>(), c->keep.as<int32_t>(), c->st),
         "mirror keep");
   return compact_into_set(c, in, set);
@@ -894,8 +901,9 @@ int check_create_args(int64_t n, double homo_ub, double lumo_lb, double tau, con
   if (prm.stop != SP2_STOP_PARAMETERLESS && prm.stop != SP2_STOP_IDEMPOTENCY) return SP2_ERR_INVALID_ARG;
   if (!(prm.fp64_tail >= 0.0) || !std::isfinite(prm.fp64_tail)) return SP2_ERR_INVALID_ARG;
   if (prm.acc_flush_min < 0) return SP2_ERR_INVALID_ARG;
-  if (prm.trunc != SP2_TRUNC_FROBENIUS && prm.trunc != SP2_TRUNC_FROBINF) return SP2_ERR_INVALID_ARG;
-  if (prm.trunc == SP2_TRUNC_FROBINF && (prm.frobinf_part < TB || prm.frobinf_part % TB)) return SP2_ERR_INVALID_ARG;
+  if (prm.trunc != SP2_TRUNC_FROBENIUS && prm.trunc != SP2_TRUNC_FROBINF && prm.trunc != SP2_TRUNC_MIXED)
+    return SP2_ERR_INVALID_ARG;
+  if (prm.trunc != SP2_TRUNC_FROBENIUS && (prm.frobinf_part < TB || prm.frobinf_part % TB)) return SP2_ERR_INVALID_ARG;
   if (prm.n_max_cap < 1 || prm.n_max_cap > SP2_MAX_ITER - 2) return SP2_ERR_INVALID_ARG;
   if (prm.precision != SP2_PREC_FP64 && prm.precision != SP2_PREC_SPLIT16) return SP2_ERR_INVALID_ARG;
   if (prm.precision == SP2_PREC_SPLIT16 && (prm.slices < 2 || prm.slices > 4)) return SP2_ERR_INVALID_ARG;
@@ -905,6 +913,10 @@ int check_create_args(int64_t n, double homo_ub, double lumo_lb, double tau, con
   if (prm.storage == SP2_STORAGE_GENERAL && prm.record_masks) return SP2_ERR_INVALID_ARG;
   const int64_t nb64 = (n + TB - 1) / TB;
   if (nb64 > 65535) return SP2_ERR_INVALID_ARG;
+  if (prm.trunc == SP2_TRUNC_MIXED) {
+    const int64_t pt = prm.frobinf_part / TB;
+    if ((nb64 + pt - 1) / pt > MIXED_MAX_BLOCKS) return SP2_ERR_INVALID_ARG;
+  }
   return SP2_OK;
 }
 
@@ -1592,10 +1604,12 @@ int sp2_truncate(const sp2_bsr* X, double tau, int32_t mode, int64_t frobinf_par
   if (!X || !keep || X->b != TB || X->n <= 0 || X->nnzb < 0 || !(tau >= 0.0) || !std::isfinite(tau))
     return SP2_ERR_INVALID_ARG;
   if (X->nnzb > 0 && (!X->brow || !X->bcol || !X->val)) return SP2_ERR_INVALID_ARG;
-  if (mode != SP2_TRUNC_FROBENIUS && mode != SP2_TRUNC_FROBINF) return SP2_ERR_INVALID_ARG;
-  if (mode == SP2_TRUNC_FROBINF && (frobinf_part < TB || frobinf_part % TB)) return SP2_ERR_INVALID_ARG;
+  if (mode != SP2_TRUNC_FROBENIUS && mode != SP2_TRUNC_FROBINF && mode != SP2_TRUNC_MIXED) return SP2_ERR_INVALID_ARG;
+  if (mode != SP2_TRUNC_FROBENIUS && (frobinf_part < TB || frobinf_part % TB)) return SP2_ERR_INVALID_ARG;
   const int64_t nb64 = (X->n + TB - 1) / TB;
   if (nb64 > 65535) return SP2_ERR_INVALID_ARG;
+  if (mode == SP2_TRUNC_MIXED && (nb64 + frobinf_part / TB - 1) / (frobinf_part / TB) > MIXED_MAX_BLOCKS)
+    return SP2_ERR_INVALID_ARG;
   if (X->nnzb == 0) return SP2_OK;
   cudaStream_t st = static_cast<cudaStream_t>(cuda_stream);
   const int nb = (int)nb64;
@@ -1628,7 +1642,9 @@ int sp2_truncate(const sp2_bsr* X, double tau, int32_t mode, int64_t frobinf_par
       bcol = static_cast<int32_t*>(dbcol);
       val = static_cast<double*>(dval);
     }
-    if (!get(&dn2, nnzb * 8) || !get(&work, trunc_work_bytes(nnzb, nb, part_tiles))) break;
+    const int nsb = (int)((nb + part_tiles - 1) / part_tiles);
+    const size_t wbytes = mode == SP2_TRUNC_MIXED ? mixed_work_bytes(nnzb, nsb) : trunc_work_bytes(nnzb, nb, part_tiles);
+    if (!get(&dn2, nnzb * 8) || !get(&work, wbytes)) break;
     int32_t* kout = keep;
     if (!dev) {
       if (!get(&dkeep, nnzb * 4)) break;
@@ -1640,7 +1656,10 @@ int sp2_truncate(const sp2_bsr* X, double tau, int32_t mode, int64_t frobinf_par
     ts.bcol = const_cast<int32_t*>(bcol);
     ts.slot = nullptr;
     if (launch_tile_norms(val, nnzb, static_cast<double*>(dn2), st) != cudaSuccess ||
-        launch_truncate(ts, static_cast<double*>(dn2), nb, tau, mode, part_tiles, work, kout, st) != cudaSuccess) {
+        (mode == SP2_TRUNC_MIXED
+             ? mixed_select(ts, static_cast<double*>(dn2), nb, tau, part_tiles, work, kout, st)
+             : launch_truncate(ts, static_cast<double*>(dn2), nb, tau, mode, part_tiles, work, kout, st)) !=
+            cudaSuccess) {
       rc = SP2_ERR_CUDA;
       break;
     }

@@ -106,6 +106,15 @@ cudaError_t launch_truncate(const TileSet& x, const double* n2, int nb, double t
 
 cudaError_t launch_tile_norms(const double* val, int64_t nnzb, double* n2, cudaStream_t st);
 
+// Mixed-norm selection (Section 3, ||.||_m on a partition of part_tiles tiles):
+// work of mixed_work_bytes(nnzb, nsb); synchronises the stream (one host round
+// trip per bisection probe).
+constexpr int MIXED_MAX_BLOCKS = 512;
+size_t mixed_work_bytes(int64_t nnzb, int nsb);
+double mixed_norm_bound_host(const unsigned long long* B2, int nsb);
+cudaError_t mixed_select(const TileSet& x, const double* n2, int nb, double tau, int64_t part_tiles, void* work,
+                         int32_t* keep, cudaStream_t st);
+
 // compact.cu
 cudaError_t launch_compact(const TileSet& in, const int32_t* keep, int nb, TileSet& out, int32_t* count_dev,
                            void* scan_tmp, int32_t* scan_buf, cudaStream_t st);

@@ -19,6 +19,9 @@
 // 8 bits; each pass histograms the budget units of the remaining candidates and
 // one thread per segment walks its 256 buckets.  No sort, no host round trip.
 // A single segment of at most 2048 tiles runs the same passes in one CTA.
+#include <cmath>
+#include <vector>
+
 #include "sp2_internal.h"
 
 namespace sp2 {
@@ -27,6 +30,7 @@ namespace {
 constexpr double Q_SCALE = 68719476736.0;          // 2^36
 constexpr unsigned long long Q_BUDGET = 1ull << 36;
 constexpr unsigned long long Q_CAP = 1ull << 37;
+constexpr int MIXED_POWER_ITERS = 100;        // power steps of the mixed-norm bound
 
 struct Work {
   unsigned long long* q;
@@ -350,6 +354,55 @@ __global__ void __launch_bounds__(256) k_tile_norms(const double* __restrict__ v
 
 inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
+
+// ---------------------------------------------------------------- mixed norm
+// Frobenius-spectral mixed norm of Section 3 on a partition of pt tiles:
+// every tile gets its budget units q (weight 2 for an off-diagonal tile inside
+// a diagonal block, units of tau^2 2^-36 rounded up, capped), the pattern of
+// its squared norm (non-negative doubles order like their bit patterns) and
+// its block index R * nsb + C.
+__global__ void k_mixed_prep(const int32_t* __restrict__ brow, const int32_t* __restrict__ bcol,
+                             const int32_t* __restrict__ slot, const double* __restrict__ n2, int64_t nnzb, int pt,
+                             int nsb, double sc, unsigned long long* q, long long* bits, int32_t* blk) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t >= nnzb) return;
+  const int I = brow[t], J = bcol[t];
+  const int R = I / pt, C = J / pt;
+  const double wt = (R == C && I != J) ? 2.0 : 1.0;
+  const double v = n2[slot ? slot[t] : t];
+  const double x = (wt * v) * sc;
+  q[t] = (x >= (double)Q_CAP) ? Q_CAP : (unsigned long long)ceil(x);
+  bits[t] = __double_as_longlong(v);
+  blk[t] = R * nsb + C;
+}
+
+// Block sums of the units of the tiles with bits <= theta (and the mirror block
+// for R != C), exact integer atomics; cnt[0] counts the tiles with
+// lo < bits <= hi (the bisection ends when none is left between its ends).
+__global__ void k_mixed_probe(const unsigned long long* __restrict__ q, const long long* __restrict__ bits,
+                              const int32_t* __restrict__ blk, int64_t nnzb, int nsb, long long theta, long long lo,
+                              long long hi, unsigned long long* B2, unsigned long long* cnt) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  bool between = false;
+  if (t < nnzb) {
+    const long long b = bits[t];
+    between = b > lo && b <= hi;
+    if (b <= theta && q[t] != 0ull) {
+      const int k = blk[t];
+      const int R = k / nsb, C = k % nsb;
+      atomicAdd(&B2[k], q[t]);
+      if (R != C) atomicAdd(&B2[C * nsb + R], q[t]);
+    }
+  }
+  const unsigned nb = __popc(__ballot_sync(0xffffffffu, between));
+  if ((threadIdx.x & 31) == 0 && nb) atomicAdd(cnt, (unsigned long long)nb);
+}
+
+__global__ void k_mixed_keep(const long long* __restrict__ bits, int64_t nnzb, long long theta, int32_t* keep) {
+  const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (t < nnzb) keep[t] = bits[t] <= theta ? 0 : 1;
+}
+
 }  // namespace
 
 cudaError_t launch_tile_norms(const double* val, int64_t nnzb, double* n2, cudaStream_t st) {
@@ -395,6 +448,105 @@ cudaError_t launch_truncate(const TileSet& x, const double* n2, int nb, double t
     { ++g_launches; k_select<<<grid_for(nseg, 128), 128, 0, st>>>(w, p); }
   }
   { ++g_launches; k_mark<<<grid_for(nnzb, 256), 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, nb, w, keep); }
+  return cudaGetLastError();
+}
+
+}  // namespace sp2
+
+namespace sp2 {
+
+// Collatz-Wielandt upper bound of rho(M), M = sqrt(B2) (nsb x nsb, symmetric,
+// non-negative): rows that are all zero are skipped; x starts at all ones and
+// MIXED_POWER_ITERS times takes u = max_i (M x)_i / x_i, then x = (M x + u x)
+// / max(M x + u x); the smallest u is returned.  Sequential row sums without
+// fused multiply-adds.
+double mixed_norm_bound_host(const unsigned long long* B2, int nsb) {
+  std::vector<int> live;
+  for (int i = 0; i < nsb; ++i) {
+    bool nz = false;
+    for (int j = 0; j < nsb && !nz; ++j) nz = B2[(size_t)i * nsb + j] != 0ull;
+    if (nz) live.push_back(i);
+  }
+  const int m = (int)live.size();
+  if (m == 0) return 0.0;
+  std::vector<double> M((size_t)m * m), x(m, 1.0), y(m);
+  for (int a = 0; a < m; ++a)
+    for (int b = 0; b < m; ++b) M[(size_t)a * m + b] = std::sqrt((double)B2[(size_t)live[a] * nsb + live[b]]);
+  double best = INFINITY;
+  for (int it = 0; it < MIXED_POWER_ITERS; ++it) {
+    for (int a = 0; a < m; ++a) {
+      double acc = 0.0;
+      for (int b = 0; b < m; ++b) {
+        const double prod = M[(size_t)a * m + b] * x[b];
+        acc = acc + prod;
+      }
+      y[a] = acc;
+    }
+    double u = 0.0;
+    for (int a = 0; a < m; ++a) u = std::max(u, y[a] / x[a]);
+    best = std::min(best, u);
+    double mx = 0.0;
+    for (int a = 0; a < m; ++a) {
+      const double ux = u * x[a];
+      y[a] = y[a] + ux;
+      mx = std::max(mx, y[a]);
+    }
+    for (int a = 0; a < m; ++a) x[a] = y[a] / mx;
+  }
+  return best;
+}
+
+size_t mixed_work_bytes(int64_t nnzb, int nsb) {
+  return align_up((size_t)nnzb * 8) * 2 + align_up((size_t)nnzb * 4) + align_up((size_t)nsb * nsb * 8) + 256;
+}
+
+// keep[t] for the mixed-norm selection (see the oracle's reading): bisection
+// over the 63-bit patterns of the squared norms for the largest theta whose
+// dropped set has a bound of at most tau (in units: 2^18); each probe is one
+// kernel and a host round trip; the bisection stops early once no tile lies
+// between its ends.  Synchronises the stream.
+cudaError_t mixed_select(const TileSet& x, const double* n2, int nb, double tau, int64_t part_tiles, void* work,
+                         int32_t* keep, cudaStream_t st) {
+  const int64_t nnzb = x.nnzb;
+  if (nnzb == 0) return cudaSuccess;
+  const int pt = (int)part_tiles;
+  const int nsb = (int)((nb + pt - 1) / pt);
+  char* p = static_cast<char*>(work);
+  unsigned long long* q = reinterpret_cast<unsigned long long*>(p); p += align_up((size_t)nnzb * 8);
+  long long* bits = reinterpret_cast<long long*>(p); p += align_up((size_t)nnzb * 8);
+  int32_t* blk = reinterpret_cast<int32_t*>(p); p += align_up((size_t)nnzb * 4);
+  unsigned long long* B2 = reinterpret_cast<unsigned long long*>(p); p += align_up((size_t)nsb * nsb * 8);
+  unsigned long long* cnt = reinterpret_cast<unsigned long long*>(p);
+  const unsigned g = grid_for(nnzb, 256);
+  const double sc = tau > 0.0 ? Q_SCALE / (tau * tau) : 0.0;
+  ++g_launches;
+  k_mixed_prep<<<g, 256, 0, st>>>(x.brow, x.bcol, x.slot, n2, nnzb, pt, nsb, sc, q, bits, blk);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  // tau = 0 keeps lo = 0: only tiles that are exactly zero are dropped
+  long long lo = 0, hi = 0x7FFFFFFFFFFFFFFFll;
+  if (tau > 0.0) {
+    std::vector<unsigned long long> h((size_t)nsb * nsb + 1);
+    const double limit = 262144.0;   // tau in units of tau 2^-18
+    while (hi - lo > 1) {
+      const long long mid = lo + (hi - lo) / 2;
+      if ((e = cudaMemsetAsync(B2, 0, (size_t)nsb * nsb * 8, st)) != cudaSuccess) return e;
+      if ((e = cudaMemsetAsync(cnt, 0, 8, st)) != cudaSuccess) return e;
+      ++g_launches;
+      k_mixed_probe<<<g, 256, 0, st>>>(q, bits, blk, nnzb, nsb, mid, lo, hi, B2, cnt);
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+      if ((e = cudaMemcpyAsync(h.data(), B2, (size_t)nsb * nsb * 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return e;
+      if ((e = cudaMemcpyAsync(h.data() + (size_t)nsb * nsb, cnt, 8, cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return e;
+      if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return e;
+      if (h[(size_t)nsb * nsb] == 0) break;   // no tile between lo and hi: the result is lo
+      if (mixed_norm_bound_host(h.data(), nsb) <= limit) lo = mid;
+      else hi = mid;
+    }
+  }
+  ++g_launches;
+  k_mixed_keep<<<g, 256, 0, st>>>(bits, nnzb, lo, keep);
   return cudaGetLastError();
 }
 

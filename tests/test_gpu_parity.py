@@ -326,3 +326,15 @@ def test_general_storage_rejects_recording_for_the_adjoint():
     with pytest.raises(sp2.SP2Error) as e:
         sp2.SP2(from_dense(d["F"]), 32, d["homo_ub"], d["lumo_lb"], 0.0, storage="general", record_masks=1)
     assert e.value.code == -1
+
+
+# ----------------------------------------------------------------- mixed-norm truncation in the expansion
+@pytest.mark.parametrize("key,part", [("2s", 512), ("4s", 1024), ("3s", 1024)])
+def test_parity_mixed_norm_truncation(key, part):
+    c = _case(key)
+    kw = dict(trunc="mixed", frobinf_part=part)
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    compare(g, o)
+    f = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], trunc="frobinf", frobinf_part=part)
+    print(f"config {key}: stored tiles of D, mixed norm {len(o.kept[o.n])}, Frob-Inf {len(f.kept[f.n])}")

@@ -83,3 +83,35 @@ def test_keep_flags_around_one_cta_limit(n, mode, tau):
     g = sp2.sp2_truncate(X, tau, mode, 4096)
     o = _oracle_keep(X, tau, mode, 4096)
     assert np.array_equal(g, o), np.nonzero(g != o)
+
+
+# ----------------------------------------------------------------- mixed norm (Section 3)
+@pytest.mark.parametrize("part", [64, 128, 4096])
+@pytest.mark.parametrize("tau", [0.0, 1e-6, 1e-3, 0.1])
+@pytest.mark.parametrize("ties", [False, True])
+def test_mixed_keep_flags_bit_exact(part, tau, ties):
+    # the same integer block sums, bisection and power-step bound on both sides
+    import paper_1909_12533_gb300 as sp2
+    X = _decaying(331, 17, ties)
+    g = sp2.sp2_truncate(X, tau, "mixed", part)
+    o = _oracle_keep(X, tau, "mixed", part)
+    assert np.array_equal(g, o), np.nonzero(g != o)
+
+
+@pytest.mark.parametrize("n,part", [(2017, 256), (4000, 128)])
+def test_mixed_keep_flags_larger_and_norm_bound(n, part):
+    # dropped error: ||E||_2 <= ||E||_m <= tau (exact mixed norm by eigvalsh)
+    import paper_1909_12533_gb300 as sp2
+    X = _decaying(n, 6)
+    tau = 1e-3
+    g = sp2.sp2_truncate(X, tau, "mixed", part)
+    o = _oracle_keep(X, tau, "mixed", part)
+    assert np.array_equal(g, o), np.nonzero(g != o)
+    Xd = to_dense(X)
+    dropped = [(i, j) for i, j, k in zip(X.brow.tolist(), X.bcol.tolist(), g.tolist()) if not k]
+    E = Xd - O.apply_drop(Xd, dropped)
+    e = np.append(np.arange(0, n, part), n)
+    k = len(e) - 1
+    Bm = np.array([[np.linalg.norm(E[e[a]:e[a + 1], e[b]:e[b + 1]]) for b in range(k)] for a in range(k)])
+    m = float(np.abs(np.linalg.eigvalsh(Bm)).max())
+    assert 0 < len(dropped) and m <= tau * (1 + 1e-12)
