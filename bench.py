@@ -48,6 +48,7 @@ WORKLOADS = {
                           "Frobenius truncation, parameterless stop"),
     "water2k": dict(key="2s", sample="2s", desc="water-like, 101 molecules, N=2424, b=32, tau=1e-6"),
     "water9k": dict(key="2m", sample="2s", desc="water-like, 400 molecules, N=9600, b=32, tau=1e-6"),
+    "water24k-t5": dict(key="3m", sample="3s", desc="water-like, 1000 molecules, N=24000, b=32, tau=1e-5"),
     "helix128k": dict(key=4, sample="4s", desc="helix-like chain, 2000 residues x 64, N=128000, tau=1e-6"),
     "dense16k": dict(key=5, sample="5s", desc="dense N=16384, gap 0.05, tau=0, idempotency stop 1e-12"),
     "dense512": dict(key=1, sample=1, desc="dense N=512, tau=0, idempotency stop 1e-12"),

@@ -154,6 +154,26 @@ __device__ __forceinline__ long long f32_int_to_ll(float x) {
   return (long long)ih * 2048 + il;
 }
 
+// The per-CTA fixed-point staging (two 128 KB slots per CTA, 38 MB in all) is
+// written and read back by the same CTA within one tile: an L2 evict_last
+// policy keeps it out of DRAM while the operand records stream past.
+__device__ __forceinline__ uint64_t policy_evict_last() {
+  uint64_t pol;
+  asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+  return pol;
+}
+
+__device__ __forceinline__ longlong2 ld_staging(const longlong2* p, uint64_t pol) {
+  long long a, b;
+  asm volatile("ld.global.L2::cache_hint.v2.s64 {%0, %1}, [%2], %3;" : "=l"(a), "=l"(b) : "l"(p), "l"(pol));
+  return make_longlong2(a, b);
+}
+
+__device__ __forceinline__ void st_staging(longlong2* p, longlong2 v, uint64_t pol) {
+  asm volatile("st.global.L2::cache_hint.v2.s64 [%0], {%1, %2}, %3;" ::"l"(p), "l"(v.x), "l"(v.y), "l"(pol)
+               : "memory");
+}
+
 // x * 2^k, exact, by exponent arithmetic on the high word; x an integer-valued
 // double (0 or |x| >= 1) and a normal result.
 __device__ __forceinline__ double int_times_pow2(double x, int k) {
@@ -862,6 +882,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       return rowptr[row] + cnt + __popc(m & ((1u << (col & 31)) - 1u));
     };
     int seg = 0;   // segments consumed
+    const uint64_t pol = policy_evict_last();
     for (int it = 0;; ++it) {
       const int b = it & 1;
       const uint32_t par = ((uint32_t)it >> 1) & 1u;
@@ -916,7 +937,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             } else {
 #pragma unroll
               for (int i = 0; i < 8; ++i) {
-                const longlong2 t2 = sp[i];
+                const longlong2 t2 = ld_staging(sp + i, pol);
                 fx[2 * i] = t2.x;
                 fx[2 * i + 1] = t2.y;
               }
@@ -932,7 +953,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
               }
             }
 #pragma unroll
-            for (int i = 0; i < 8; ++i) sp[i] = make_longlong2(fx[2 * i], fx[2 * i + 1]);
+            for (int i = 0; i < 8; ++i) st_staging(sp + i, make_longlong2(fx[2 * i], fx[2 * i + 1]), pol);
           }
         }
         // this warp's TMEM reads of the segment are complete
@@ -977,7 +998,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           const longlong2* sp = reinterpret_cast<const longlong2*>(scr + col0);
 #pragma unroll
           for (int i = 0; i < 8; ++i) {
-            const longlong2 t2 = sp[i];
+            const longlong2 t2 = ld_staging(sp + i, pol);
             fx[2 * i] = t2.x;
             fx[2 * i + 1] = t2.y;
           }

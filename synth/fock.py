@@ -292,6 +292,8 @@ CONFIGS = {
     # reduced versions of the same recipes, small enough for the CPU oracle
     "2s": dict(kind="water", nmol=101, tau=1e-6, stop="parameterless"),
     "2m": dict(kind="water", nmol=400, tau=1e-6, stop="parameterless"),
+    # the precision form's threshold on 1000 molecules (profiling size)
+    "3m": dict(kind="water", nmol=1000, tau=1e-5, stop="parameterless"),
     "3s": dict(kind="water", nmol=203, tau=1e-5, stop="parameterless"),
     "4s": dict(kind="helix", nres=64, tau=1e-6, stop="parameterless"),
     "5s": dict(kind="dense", n=1000, nocc=500, occ=(-2.0, -0.025), virt=(0.025, 3.0), tau=0.0, stop="idempotency"),
