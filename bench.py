@@ -208,6 +208,8 @@ def main(argv=None) -> int:
     ap.add_argument("--workload", default=DEFAULT_WORKLOAD, choices=sorted(WORKLOADS))
     ap.add_argument("--precision", default="split16", choices=["fp64", "split16"])
     ap.add_argument("--slices", type=int, default=4)
+    ap.add_argument("--split-supply", type=int, default=None, choices=[0, 1],
+                    help="tensor path: B slices through copy warps (1) or bulk copies only (0); default: library")
     ap.add_argument("--storage", default="symmetric", choices=["symmetric", "general"],
                     help="general: both triangles stored and computed (the paper's general-matrix form)")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the timed FP64 reference run")
@@ -241,10 +243,11 @@ def main(argv=None) -> int:
         val = torch.from_numpy(Fh.val).cuda()
 
     stream = torch.cuda.current_stream()
+    extra = {} if args.split_supply is None else {"split_supply": args.split_supply}
 
     def step(F, precision, keep_D=False):
         ctx = sp2.SP2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision=precision,
-                      slices=args.slices, storage=args.storage)
+                      slices=args.slices, storage=args.storage, **extra)
         st = ctx.run()
         D = ctx.D_device() if keep_D else None
         ctx.close()
@@ -320,7 +323,7 @@ def main(argv=None) -> int:
 
         def e2e_step():
             ctx = sp2.SP2(HostF, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"],
-                          precision=args.precision, slices=args.slices, storage=args.storage)
+                          precision=args.precision, slices=args.slices, storage=args.storage, **extra)
             st = ctx.run()
             out = ctx.D_host(Dh)
             ctx.close()

@@ -149,6 +149,10 @@ typedef struct {
                               context are unaffected.                                   */
   int32_t storage;         /* sp2_storage, default SYMMETRIC; GENERAL does not record masks for
                               sp2_backward (record_masks must be 0)                    */
+  int32_t split_supply;    /* SPLIT16: 1 = the B operand slices of the tensor-core square reach
+                              shared memory through two copy warps (16-byte cp.async) while
+                              the A slices come by bulk copy; 0 = bulk copies only.  Same
+                              results either way; default 0                            */
 } sp2_params;
 
 typedef struct {

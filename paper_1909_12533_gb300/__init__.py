@@ -49,7 +49,7 @@ class sp2_params(ctypes.Structure):
                 ("precision", c_int32), ("slices", c_int32), ("mixed_from", c_int32), ("mixed_until", c_int32),
                 ("ckpt_every", c_int32), ("record_masks", c_int32), ("fp64_tail", c_double),
                 ("acc_flush_min", c_int32), ("wait_limit_ms", c_int32), ("selftest", c_int32),
-                ("storage", c_int32)]
+                ("storage", c_int32), ("split_supply", c_int32)]
 
 
 class sp2_stats(ctypes.Structure):

@@ -756,6 +756,7 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   L.scratch = c->tcscratch.p;
   L.seg_min = c->prm.acc_flush_min;
   L.wait_ns = (unsigned long long)c->prm.wait_limit_ms * 1000000ull;
+  L.split_supply = c->prm.split_supply != 0;
   L.selftest = c->selftest_pending == 1;
   if (c->selftest_pending == 1) c->selftest_pending = 0;
   L.err = c->errflag.as<int32_t>();
@@ -828,6 +829,7 @@ int sp2_default_params(sp2_params* p) {
   p->wait_limit_ms = 2000;
   p->selftest = 0;
   p->storage = SP2_STORAGE_SYMMETRIC;
+  p->split_supply = 0;
   return SP2_OK;
 }
 
@@ -910,6 +912,7 @@ int check_create_args(int64_t n, double homo_ub, double lumo_lb, double tau, con
   if (prm.ckpt_every < 1) return SP2_ERR_INVALID_ARG;
   if (prm.wait_limit_ms < 1 || prm.selftest < 0 || prm.selftest > 2) return SP2_ERR_INVALID_ARG;
   if (prm.storage != SP2_STORAGE_SYMMETRIC && prm.storage != SP2_STORAGE_GENERAL) return SP2_ERR_INVALID_ARG;
+  if (prm.split_supply != 0 && prm.split_supply != 1) return SP2_ERR_INVALID_ARG;
   if (prm.storage == SP2_STORAGE_GENERAL && prm.record_masks) return SP2_ERR_INVALID_ARG;
   const int64_t nb64 = (n + TB - 1) / TB;
   if (nb64 > 65535) return SP2_ERR_INVALID_ARG;

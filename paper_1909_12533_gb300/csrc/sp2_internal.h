@@ -184,6 +184,7 @@ struct TcLaunch {
   unsigned long long wait_ns = 2000000000ull;   // limit of every bounded wait in the kernel
   bool selftest = false;     // wait first on a barrier nothing arrives at (tests the timeout path)
   bool general = false;      // general storage: every output tile of the square, weight 1 in e^2
+  bool split_supply = false; // B operand units through copy warps (cp.async) beside the bulk copies of A
 };
 size_t panel_record_bytes(int k);
 // report_range: also report an out-of-range element (error bit 4) without one

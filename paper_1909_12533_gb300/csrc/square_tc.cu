@@ -105,7 +105,7 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
 }
 
 // Timeout sites of a launch, for the error message (err[1], bit 0 self-test
-// probe, 1 producer stage, 2 producer tile slot, 3 MMA data, 4 MMA TMEM or segment slot, 5 MMA
+// probe, 8 copy warps, 1 producer stage, 2 producer tile slot, 3 MMA data, 4 MMA TMEM or segment slot, 5 MMA
 // drain, 6 epilogue tile, 7 epilogue segment).
 __device__ __forceinline__ void note_timeout(int32_t* err, int where) {
   if (err) atomicOr(err + 1, 1 << where);
@@ -426,6 +426,7 @@ struct TcArgs {
   unsigned long long wait_ns;   // limit of every bounded wait
   int selftest;             // 1: the producer first waits on a barrier nothing arrives at (timeout path test)
   int general;              // general storage: output tiles on both sides of the diagonal, weight 1 in e^2
+  int split_supply;         // 1: the B units come through the copy warps (cp.async), the A units by bulk copy
 };
 
 // A pipeline stage holds one sub-step: two A units and two B units, a unit
@@ -444,7 +445,8 @@ constexpr int STAGE_BYTES = 4 * UNIT_BYTES;
 constexpr int STAGES = 6;
 constexpr uint32_t REC_END = 1u << 12;
 constexpr int EPI_WARPS = 8;                       // epilogue warps 2..9
-constexpr int TC_THREADS = 32 * (2 + EPI_WARPS);   // + producer warp 0, MMA warp 1
+constexpr int COPY_WARPS = 2;                      // copy warps 10..11 (B units by 16-byte cp.async)
+constexpr int TC_THREADS = 32 * (2 + EPI_WARPS + COPY_WARPS);   // + producer warp 0, MMA warp 1
 constexpr uint32_t REC_LAST = 1u << 13;   // no more super-tiles (no data)
 constexpr uint32_t REC_SEG = 1u << 14;    // end of an accumulation segment of the super-tile (no data)
 constexpr uint32_t SEG_LAST = 1u << 31;   // segment record flag: last segment of its super-tile
@@ -475,7 +477,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   uint64_t* drain = tile_empty + 2;        // MMAs issued before the exit are complete
   uint64_t* tmem_empty = drain + 1;        // [SEG_RING] every epilogue warp has read the segment's TMEM
   uint64_t* probe = tmem_empty + SEG_RING; // self-test: a barrier that nothing arrives at
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(probe + 1);
+  uint64_t* fill = probe + 1;              // [STAGES] stage record written: the copy warps may fill B
+  const __half** srcb = reinterpret_cast<const __half**>(fill + STAGES);   // [STAGES] B record of the stage
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(srcb + STAGES);
   int32_t* tslot = reinterpret_cast<int32_t*>(tmem_slot + 2);      // [2] super-tile list index, -1: none
   int32_t* kcount = tslot + 2;                                      // [2][16] triplets per output tile
   uint32_t* gmap = reinterpret_cast<uint32_t*>(kcount + 32);       // [SEG_RING] groups written, block of each, last flag
@@ -486,8 +490,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      mbar_init(&full[s], 1);
+      // the producer's arrival (with the bulk bytes), plus one per copy-warp thread
+      mbar_init(&full[s], 1 + (a.split_supply ? 32 * COPY_WARPS : 0));
       mbar_init(&empty[s], 1);
+      mbar_init(&fill[s], 1);
     }
     for (int b = 0; b < SEG_RING; ++b) {
       mbar_init(&acc_full[b], 2);
@@ -546,17 +552,21 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
         return false;
       }
       const uint32_t mask = (rv & (REC_END | REC_LAST | REC_SEG)) ? 0u : (rv >> 8) & 0xFu;
-      // units A0, A1, B0, B1 read by a product of the mask
-      const uint32_t use = ((mask & 0x3u) ? 1u : 0u) | ((mask & 0xCu) ? 2u : 0u) | ((mask & 0x5u) ? 4u : 0u) |
-                           ((mask & 0xAu) ? 8u : 0u);
+      // units A0, A1, B0, B1 read by a product of the mask; with the split
+      // supply the B units go to the copy warps
+      uint32_t use = ((mask & 0x3u) ? 1u : 0u) | ((mask & 0xCu) ? 2u : 0u) | ((mask & 0x5u) ? 4u : 0u) |
+                     ((mask & 0xAu) ? 8u : 0u);
+      if (a.split_supply) use &= 0x3u;
       if (lane == 0) {
         rec[s] = rv;
+        srcb[s] = srcB;
         mbar_expect_tx(&full[s], (uint32_t)__popc(use) * UNIT_BYTES);
       }
       if ((use >> lane) & 1u)
         bulk_g2s(stage_base + s * STAGE_BYTES + lane * UNIT_BYTES,
                  (lane < 2 ? srcA : srcB) + (int64_t)((rv >> (2 * lane)) & 3u) * (UNIT_BYTES / 2), UNIT_BYTES,
                  &full[s]);
+      if (a.split_supply && lane == 0) mbar_arrive(&fill[s]);   // release: record and B source visible
       return true;
     };
     // all lanes: a control sub-step (no data) through lanes 0-3
@@ -758,7 +768,6 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
     // a free block on its first product, and the blocks of a segment return to
     // the pool once every epilogue warp has read them (one arrival per warp on
     // the segment slot's tmem_empty barrier; segments are reclaimed in order).
-    int step = 0;
     uint32_t free_mask = 0xFu;
     // blocks held by the segment in each ring slot (4 slots)
     uint32_t pend0 = 0u, pend1 = 0u, pend2 = 0u, pend3 = 0u;
@@ -782,22 +791,30 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       ++released;
       return true;
     };
+    // stage counter and phase kept incrementally; the shared-memory descriptor
+    // of a unit is the stage's descriptor plus a constant (the start-address
+    // field holds address / 16 in 14 bits; every address here is below 2^18)
+    int s = 0;
+    uint32_t par = 0;
+    const uint64_t d0 = make_desc(smem_u32(stage_base), 128, 512);
     while (ok && !done) {
       uint32_t written = 0, gblk = 0, used = 0;
       uint32_t kind = 0;
       for (;;) {
-        const int s = step % STAGES;
-        const uint32_t par = (step / STAGES) & 1;
-        ++step;
-        if (!mbar_wait(&full[s], par)) { ok = false; note_timeout(a.err, 3); break; }
+        const int cs = s;
+        const uint32_t cpar = par;
+        if (++s == STAGES) { s = 0; par ^= 1u; }
+        if (!mbar_wait(&full[cs], cpar)) { ok = false; note_timeout(a.err, 3); break; }
         tc_fence_after();
-        const uint32_t rv = rec[s];
+        // units written by cp.async (generic proxy) are read by the MMAs (async proxy)
+        if (a.split_supply) asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        const uint32_t rv = rec[cs];
         if (rv & (REC_END | REC_LAST | REC_SEG)) {
-          mma_commit(&empty[s]);
+          mma_commit(&empty[cs]);
           kind = rv & (REC_END | REC_LAST | REC_SEG);
           break;
         }
-        const uint32_t sbase = smem_u32(stage_base + s * STAGE_BYTES);
+        const uint64_t ds = d0 + (uint64_t)(cs * (STAGE_BYTES >> 4));
 #pragma unroll
         for (int i = 0; i < 2; ++i) {
 #pragma unroll
@@ -816,8 +833,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             const uint32_t acc = (written >> g) & 1u;
 #pragma unroll
             for (int kk = 0; kk < 2; ++kk) {
-              const uint64_t ad = make_desc(sbase + i * UNIT_BYTES + kk * 256, 128, 512);
-              const uint64_t bd = make_desc(sbase + (2 + j) * UNIT_BYTES + kk * 256, 128, 512);
+              const uint64_t ad = ds + (uint64_t)((i * UNIT_BYTES + kk * 256) >> 4);
+              const uint64_t bd = ds + (uint64_t)(((2 + j) * UNIT_BYTES + kk * 256) >> 4);
               // the first MMA into a group accumulator of a segment overwrites it
               mma_f16(dcol, ad, bd, (kk > 0 || acc) ? 1u : 0u);
             }
@@ -826,7 +843,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           }
           if (!ok) break;
         }
-        mma_commit(&empty[s]);
+        mma_commit(&empty[cs]);
         if (!ok) break;
       }
       if (!ok) break;
@@ -852,6 +869,51 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
     if (a.err && nprod) atomicAdd(reinterpret_cast<unsigned long long*>(a.err + 2), nprod);
     mma_commit(drain);
     if (!mbar_wait(drain, 0)) { status[0] = 1; note_timeout(a.err, 5); }
+  } else if (warp >= 2 + EPI_WARPS) {
+    // ---------------- copy warps (split supply only).  Stage by stage, in the
+    // producer's order: wait until the producer has written the stage record
+    // (fill), copy the B units the record uses as 16-byte cp.async pieces (the
+    // 64 threads take every 64th piece of an 8 KB unit), then arrive on the
+    // stage's full barrier when this thread's copies have landed.  Control
+    // records carry no data but are arrived at all the same.
+    if (a.split_supply) {
+      const int t = threadIdx.x - 32 * (2 + EPI_WARPS);   // 0 .. 63
+      int ns = 0;
+      uint32_t npar = 0;
+      for (;;) {
+        const int s = ns;
+        const uint32_t par = npar;
+        if (++ns == STAGES) { ns = 0; npar ^= 1u; }
+        bool good = true;
+        if (lane == 0) good = mbar_wait_sleep(&fill[s], par);
+        good = __shfl_sync(FULLW, good ? 1 : 0, 0) != 0;
+        if (!good) {
+          if (lane == 0) {
+            status[0] = 1;
+            note_timeout(a.err, 8);
+          }
+          break;
+        }
+        const uint32_t rv = rec[s];
+        if (!(rv & (REC_END | REC_LAST | REC_SEG))) {
+          const uint32_t mask = (rv >> 8) & 0xFu;
+          const __half* srcB = srcb[s];
+#pragma unroll
+          for (int j = 0; j < 2; ++j) {
+            if (!(mask & (j == 0 ? 0x5u : 0xAu))) continue;
+            const char* src = reinterpret_cast<const char*>(srcB + (int64_t)((rv >> (4 + 2 * j)) & 3u) * (UNIT_BYTES / 2));
+            const uint32_t dst = smem_u32(stage_base + s * STAGE_BYTES + (2 + j) * UNIT_BYTES);
+#pragma unroll
+            for (int c = t; c < UNIT_BYTES / 16; c += 32 * COPY_WARPS)
+              asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(dst + 16 * c), "l"(src + 16 * c)
+                           : "memory");
+          }
+        }
+        asm volatile("cp.async.mbarrier.arrive.noinc.shared::cta.b64 [%0];" ::"r"(smem_u32(&full[s])) : "memory");
+        if (rv & REC_LAST) break;
+      }
+      asm volatile("cp.async.wait_all;" ::: "memory");
+    }
   } else if (warp >= 2) {
     // ---------------- epilogue (warps 2-9, two per SM sub-partition: warp w
     // reads TMEM lanes 32 (w % 4)..+31 = tile row I0 + w % 4, lane = row inside
@@ -1192,6 +1254,7 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   a.wait_ns = L.wait_ns;
   a.selftest = L.selftest ? 1 : 0;
   a.general = L.general ? 1 : 0;
+  a.split_supply = L.split_supply ? 1 : 0;
   cudaError_t e = cudaSuccess;
   switch (L.k) {
     case 2:

@@ -139,3 +139,18 @@ def test_split16_fp64_tail_reaches_idempotency_tolerance():
     g0 = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision="split16",
                  slices=4, fp64_tail=0.0, n_max_cap=20)
     assert all(p == 1 for p in g0["stats"]["prec_hist"])
+
+
+@pytest.mark.parametrize("key,extra", [(1, {}), ("2s", {}), ("3s", {}), ("4s", {}),
+                                       ("5s", {"acc_flush_min": 1}), ("2s", {"storage": "general"})])
+def test_split_supply_gives_the_same_result(key, extra):
+    # the B slices through the copy warps (cp.async) instead of bulk copies: the
+    # same bytes land in the same stages, so D is the same bit for bit
+    c = make_config(key)
+    kw = dict(stop=c["stop"], precision="split16", slices=4, **extra)
+    a = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], split_supply=0, **kw)
+    b = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], split_supply=1, **kw)
+    assert a["code"] == 0 and b["code"] == 0
+    assert a["stats"]["n"] == b["stats"]["n"]
+    assert np.array_equal(a["brow"], b["brow"]) and np.array_equal(a["val"], b["val"])
+    assert a["stats"]["e"] == b["stats"]["e"]

@@ -22,6 +22,10 @@ def _decaying(n, seed, ties=False):
         src = X.val[off[3]].copy()
         for k in off[5:40:3]:
             X.val[k] = src * 1e-3
+        # rows and columns past n are padding and stay zero
+        r0 = n - 32 * (X.nb - 1)
+        X.val[X.bcol == X.nb - 1, :, r0:] = 0.0
+        X.val[X.brow == X.nb - 1, r0:, :] = 0.0
     return X
 
 
