@@ -210,6 +210,9 @@ def main(argv=None) -> int:
     ap.add_argument("--slices", type=int, default=4)
     ap.add_argument("--split-supply", type=int, default=None, choices=[0, 1],
                     help="tensor path: B slices through copy warps (1) or bulk copies only (0); default: library")
+    ap.add_argument("--fp64-tail", type=float, default=None,
+                    help="tensor path with the idempotency stop: FP64 squares once e_j < this (0: none); "
+                         "default: library")
     ap.add_argument("--storage", default="symmetric", choices=["symmetric", "general"],
                     help="general: both triangles stored and computed (the paper's general-matrix form)")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the timed FP64 reference run")
@@ -244,6 +247,8 @@ def main(argv=None) -> int:
 
     stream = torch.cuda.current_stream()
     extra = {} if args.split_supply is None else {"split_supply": args.split_supply}
+    if args.fp64_tail is not None:
+        extra["fp64_tail"] = args.fp64_tail
 
     def step(F, precision, keep_D=False):
         ctx = sp2.SP2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision=precision,

@@ -80,7 +80,12 @@ enum sp2_trunc     { SP2_TRUNC_FROBENIUS = 0, SP2_TRUNC_FROBINF = 1, SP2_TRUNC_M
  *            grids (slice s on the grid 2^-(11 s - 1)); products of slice pairs
  *            (s, t) with s + t <= slices + 1 accumulate exactly-grouped in FP32
  *            tensor memory and are combined in FP64.  slices = 2 is the
- *            hi+lo three-product form.
+ *            hi+lo three-product form; slices = 5 (finest grid 2^-54,
+ *            FP64-grade) runs each square as two launches: the finest group
+ *            (s + t = 6) first, its exact sum left in the output tiles, then
+ *            the other four groups added to it in the full epilogue (tensor
+ *            memory holds four group accumulators); it does not record masks
+ *            for sp2_backward.
  * Everything else (traces, norms, polynomial choice, stop test, truncation)
  * is FP64 in every precision. */
 enum sp2_precision { SP2_PREC_FP64 = 0, SP2_PREC_SPLIT16 = 1 };
@@ -123,7 +128,7 @@ typedef struct {
   double delta_acc;        /* acceleration switches off once max distance <= delta_acc; default 0.1 */
   int32_t n_max_cap;       /* cap on n_max, <= SP2_MAX_ITER - 2; default 100             */
   int32_t precision;       /* sp2_precision, default FP64                               */
-  int32_t slices;          /* SPLIT16 slices, 2..4, default 4                            */
+  int32_t slices;          /* SPLIT16 slices, 2..5, default 4                            */
   int32_t mixed_from;      /* first iteration i whose square uses `precision` (earlier ones FP64); default 1 */
   int32_t mixed_until;     /* last iteration using `precision` (later ones FP64); 0 = no limit */
   int32_t ckpt_every;      /* adjoint checkpoint interval k (X~_i kept for i % k == 0); default 8 */

@@ -760,6 +760,21 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   L.selftest = c->selftest_pending == 1;
   if (c->selftest_pending == 1) c->selftest_pending = 0;
   L.err = c->errflag.as<int32_t>();
+  if (c->prm.slices == 5 && !L.two_pass) {
+    // five slices: the finest group (s + t = 4) first, its exact sum left in
+    // the output tiles; then groups 0-3, added to it in the full epilogue
+    // (TMEM holds four group accumulators at a time)
+    c->ck(cudaEventRecord(c->evs0, c->st), "event");
+    TcLaunch Lf = L;
+    Lf.glo = 4; Lf.ghi = 4; Lf.emode = 1;
+    c->ck(launch_square_tc(Lf, c->st), "square tc (finest group)");
+    c->ck(cudaMemsetAsync(c->scount.as<int32_t>() + 1, 0, 4, c->st), "memset");
+    TcLaunch Lm = L;
+    Lm.glo = 0; Lm.ghi = 3; Lm.emode = 2;
+    c->ck(launch_square_tc(Lm, c->st), "square tc");
+    c->ck(cudaEventRecord(c->evs1, c->st), "event");
+    return;
+  }
   c->ck(cudaEventRecord(c->evs0, c->st), "event");
   c->ck(launch_square_tc(L, c->st), "square tc");
   c->ck(cudaEventRecord(c->evs1, c->st), "event");
@@ -908,7 +923,8 @@ int check_create_args(int64_t n, double homo_ub, double lumo_lb, double tau, con
   if (prm.trunc != SP2_TRUNC_FROBENIUS && (prm.frobinf_part < TB || prm.frobinf_part % TB)) return SP2_ERR_INVALID_ARG;
   if (prm.n_max_cap < 1 || prm.n_max_cap > SP2_MAX_ITER - 2) return SP2_ERR_INVALID_ARG;
   if (prm.precision != SP2_PREC_FP64 && prm.precision != SP2_PREC_SPLIT16) return SP2_ERR_INVALID_ARG;
-  if (prm.precision == SP2_PREC_SPLIT16 && (prm.slices < 2 || prm.slices > 4)) return SP2_ERR_INVALID_ARG;
+  if (prm.precision == SP2_PREC_SPLIT16 && (prm.slices < 2 || prm.slices > 5)) return SP2_ERR_INVALID_ARG;
+  if (prm.precision == SP2_PREC_SPLIT16 && prm.slices == 5 && prm.record_masks) return SP2_ERR_INVALID_ARG;
   if (prm.ckpt_every < 1) return SP2_ERR_INVALID_ARG;
   if (prm.wait_limit_ms < 1 || prm.selftest < 0 || prm.selftest > 2) return SP2_ERR_INVALID_ARG;
   if (prm.storage != SP2_STORAGE_SYMMETRIC && prm.storage != SP2_STORAGE_GENERAL) return SP2_ERR_INVALID_ARG;

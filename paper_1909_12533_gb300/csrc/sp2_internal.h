@@ -185,6 +185,8 @@ struct TcLaunch {
   bool selftest = false;     // wait first on a barrier nothing arrives at (tests the timeout path)
   bool general = false;      // general storage: every output tile of the square, weight 1 in e^2
   bool split_supply = false; // B operand units through copy warps (cp.async) beside the bulk copies of A
+  int glo = 0, ghi = -1;     // slice-pair groups s + t of the launch (ghi < 0: all, k - 1; at most 4 groups)
+  int emode = 0;             // 0 full epilogue, 1 store S only, 2 full epilogue on S + the stored S
 };
 size_t panel_record_bytes(int k);
 // report_range: also report an out-of-range element (error bit 4) without one

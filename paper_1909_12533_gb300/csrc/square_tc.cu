@@ -427,14 +427,17 @@ struct TcArgs {
   int selftest;             // 1: the producer first waits on a barrier nothing arrives at (timeout path test)
   int general;              // general storage: output tiles on both sides of the diagonal, weight 1 in e^2
   int split_supply;         // 1: the B units come through the copy warps (cp.async), the A units by bulk copy
+  int glo, ghi;             // slice-pair groups s + t of this launch (ghi - glo <= 3)
+  int emode;                // 0: full epilogue; 1: write S (this launch's groups) into the output tiles only;
+                            // 2: full epilogue on S + the S already in the output tiles
 };
 
 // A pipeline stage holds one sub-step: two A units and two B units, a unit
 // being one slice of a 4-tile panel (128 rows x 32, 8 KB, 8-row groups 512 B
 // apart).  A sub-step record (32 bits) tells the MMA issuer what it holds:
-//   bits 0-1 / 2-3: slices of A units 0 / 1, bits 4-5 / 6-7: of B units 0 / 1,
-//   bits 8-11: product mask, bit (2 i + j) for A unit i x B unit j,
-//   bit 12: end of the super-tile, bit 13: no more super-tiles, bit 14: end of an
+//   bits 3u..3u+2: slice of unit u (u = 0, 1: A units, u = 2, 3: B units),
+//   bits 12-15: product mask, bit (2 i + j) for A unit i x B unit j,
+//   bit 16: end of the super-tile, bit 17: no more super-tiles, bit 18: end of an
 //   accumulation segment (no data).  A super-tile whose K loop has at least
 //   seg_min K steps closes a segment after every 16 K steps: the epilogue adds
 //   the segment's exact fixed-point sums into the scratch and frees the TMEM,
@@ -443,12 +446,12 @@ struct TcArgs {
 constexpr int UNIT_BYTES = 4 * SLICE_BYTES;
 constexpr int STAGE_BYTES = 4 * UNIT_BYTES;
 constexpr int STAGES = 6;
-constexpr uint32_t REC_END = 1u << 12;
+constexpr uint32_t REC_END = 1u << 16;
 constexpr int EPI_WARPS = 8;                       // epilogue warps 2..9
 constexpr int COPY_WARPS = 2;                      // copy warps 10..11 (B units by 16-byte cp.async)
 constexpr int TC_THREADS = 32 * (2 + EPI_WARPS + COPY_WARPS);   // + producer warp 0, MMA warp 1
-constexpr uint32_t REC_LAST = 1u << 13;   // no more super-tiles (no data)
-constexpr uint32_t REC_SEG = 1u << 14;    // end of an accumulation segment of the super-tile (no data)
+constexpr uint32_t REC_LAST = 1u << 17;   // no more super-tiles (no data)
+constexpr uint32_t REC_SEG = 1u << 18;    // end of an accumulation segment of the super-tile (no data)
 constexpr uint32_t SEG_LAST = 1u << 31;   // segment record flag: last segment of its super-tile
 constexpr int SEG_RING = 4;               // accumulation segments in flight between MMA and epilogue
 constexpr int SEG_KSTEPS = 16;            // K steps per accumulation segment of a segmented tile
@@ -551,7 +554,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
         }
         return false;
       }
-      const uint32_t mask = (rv & (REC_END | REC_LAST | REC_SEG)) ? 0u : (rv >> 8) & 0xFu;
+      const uint32_t mask = (rv & (REC_END | REC_LAST | REC_SEG)) ? 0u : (rv >> 12) & 0xFu;
       // units A0, A1, B0, B1 read by a product of the mask; with the split
       // supply the B units go to the copy warps
       uint32_t use = ((mask & 0x3u) ? 1u : 0u) | ((mask & 0xCu) ? 2u : 0u) | ((mask & 0x5u) ? 4u : 0u) |
@@ -564,7 +567,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       }
       if ((use >> lane) & 1u)
         bulk_g2s(stage_base + s * STAGE_BYTES + lane * UNIT_BYTES,
-                 (lane < 2 ? srcA : srcB) + (int64_t)((rv >> (2 * lane)) & 3u) * (UNIT_BYTES / 2), UNIT_BYTES,
+                 (lane < 2 ? srcA : srcB) + (int64_t)((rv >> (3 * lane)) & 7u) * (UNIT_BYTES / 2), UNIT_BYTES,
                  &full[s]);
       if (a.split_supply && lane == 0) mbar_arrive(&fill[s]);   // release: record and B source visible
       return true;
@@ -698,19 +701,25 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
               const int c16 = __popc(__ballot_sync(FULLW, (pa4 >> (t >> 2)) & (pb4 >> (t & 3)) & 1u));
               if (lane == t) kc += c16;
             }
-            // sub-steps of this lane's K step: pairs s >= fa, t >= fb, s + t <= K - 1,
-            // two A and two B slices each (at most three for K = 4)
+            // sub-steps of this lane's K step: pairs s >= fa, t >= fb with
+            // glo <= s + t <= ghi (the launch's group window), two A and two B
+            // slices each; the B pair starts where A slice a0 + 1 meets glo
+            // (at most three sub-steps for every window used)
             const int fa = (int)(ha & 7u), fb = (int)(hb & 7u);
             uint32_t rv0 = 0u, rv1 = 0u, rv2 = 0u;
             int ns = 0;
-            for (int a0 = fa; a0 + fb <= K - 1; a0 += 2) {
-              for (int b0 = fb; a0 + b0 <= K - 1; b0 += 2) {
+            for (int a0 = fa; a0 <= K - 1 && a0 + fb <= a.ghi; a0 += 2) {
+              for (int b0 = max(fb, a.glo - a0 - 1); b0 <= K - 1 && a0 + b0 <= a.ghi; b0 += 2) {
                 uint32_t mask = 0;
                 for (int i = 0; i < 2; ++i)
-                  for (int jj = 0; jj < 2; ++jj)
-                    if (a0 + i + b0 + jj <= K - 1) mask |= 1u << (2 * i + jj);
-                const uint32_t rv = (uint32_t)a0 | ((uint32_t)min(a0 + 1, K - 1) << 2) | ((uint32_t)b0 << 4) |
-                                    ((uint32_t)min(b0 + 1, K - 1) << 6) | (mask << 8);
+                  for (int jj = 0; jj < 2; ++jj) {
+                    const int si = a0 + i, tj = b0 + jj;
+                    if (si <= K - 1 && tj <= K - 1 && si + tj >= a.glo && si + tj <= a.ghi)
+                      mask |= 1u << (2 * i + jj);
+                  }
+                if (!mask) continue;
+                const uint32_t rv = (uint32_t)a0 | ((uint32_t)min(a0 + 1, K - 1) << 3) | ((uint32_t)b0 << 6) |
+                                    ((uint32_t)min(b0 + 1, K - 1) << 9) | (mask << 12);
                 if (ns == 0) rv0 = rv;
                 else if (ns == 1) rv1 = rv;
                 else rv2 = rv;
@@ -819,8 +828,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
         for (int i = 0; i < 2; ++i) {
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
-            if (!((rv >> (8 + 2 * i + j)) & 1u)) continue;
-            const int g = (int)((rv >> (2 * i)) & 3u) + (int)((rv >> (4 + 2 * j)) & 3u);
+            if (!((rv >> (12 + 2 * i + j)) & 1u)) continue;
+            // group relative to the launch's window (at most four groups live)
+            const int g = (int)((rv >> (3 * i)) & 7u) + (int)((rv >> (6 + 3 * j)) & 7u) - a.glo;
             if (!((written >> g) & 1u)) {
               while (free_mask == 0u && ok) ok = reclaim();
               if (!ok) break;
@@ -896,12 +906,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
         }
         const uint32_t rv = rec[s];
         if (!(rv & (REC_END | REC_LAST | REC_SEG))) {
-          const uint32_t mask = (rv >> 8) & 0xFu;
+          const uint32_t mask = (rv >> 12) & 0xFu;
           const __half* srcB = srcb[s];
 #pragma unroll
           for (int j = 0; j < 2; ++j) {
             if (!(mask & (j == 0 ? 0x5u : 0xAu))) continue;
-            const char* src = reinterpret_cast<const char*>(srcB + (int64_t)((rv >> (4 + 2 * j)) & 3u) * (UNIT_BYTES / 2));
+            const char* src = reinterpret_cast<const char*>(srcB + (int64_t)((rv >> (6 + 3 * j)) & 7u) * (UNIT_BYTES / 2));
             const uint32_t dst = smem_u32(stage_base + s * STAGE_BYTES + (2 + j) * UNIT_BYTES);
 #pragma unroll
             for (int c = t; c < UNIT_BYTES / 16; c += 32 * COPY_WARPS)
@@ -924,7 +934,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
     const int quarter = warp & 3;
     const int bt0 = 2 * ((warp - 2) >> 2);
     const int r = lane;
-    const double su = Cfg::UNIT * a.scale;   // S = fx * su, su a power of two
+    // unit of the finest group of the window: slice s lies on the grid
+    // 2^-(11 s + 10), so group g = s + t has the unit 2^-(11 g + 20)
+    const double su = ldexp(1.0, -(11 * a.ghi + 20)) * a.scale;   // S = fx * su, su a power of two
     const int lsu = ilogb(su);
     // X_new = c0 I + c1 X~ + c2 S.  Without acceleration (alpha = 1) the two
     // polynomials need fewer FP64 operations, with the same results:
@@ -1005,13 +1017,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
               }
             }
 #pragma unroll
-            for (int gg = 0; gg < K; ++gg) {
-              if ((written >> gg) & 1u) {   // warp-uniform: groups no product reached are zero
+            for (int gg = 0; gg < 4; ++gg) {   // relative groups of the window
+              if (gg <= a.ghi - a.glo && ((written >> gg) & 1u)) {   // warp-uniform: groups no product reached are zero
                 float g[16];
                 const uint32_t blk = (gm >> (8 + 2 * gg)) & 3u;
                 tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + blk * ST + (uint32_t)col0, g);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) fx[i] += f32_int_to_ll(g[i]) * (1ll << (11 * (K - 1 - gg)));
+                for (int i = 0; i < 16; ++i) fx[i] += f32_int_to_ll(g[i]) * (1ll << (11 * (a.ghi - a.glo - gg)));
               }
             }
 #pragma unroll
@@ -1035,7 +1047,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
         if (oi < 0) continue;
         // Z_IJ (X~_IJ in the forward step; absent -> 0)
         const double* Zt = nullptr;
-        const int zp = find(a.zbits, a.zrowptr, Ia, Jb);
+        const int zp = a.emode == 1 ? -1 : find(a.zbits, a.zrowptr, Ia, Jb);
         if (zp >= 0) {
           const int64_t zi = (int64_t)(a.zref[zp] & ~REF_T);
           Zt = a.zpool + (int64_t)(a.zslot ? a.zslot[zi] : zi) * TE;
@@ -1064,6 +1076,19 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             fx[2 * i] = t2.x;
             fx[2 * i + 1] = t2.y;
           }
+          // emode 2: the finer groups' S, left in the output tile by the launch before
+          double prev[16];
+#pragma unroll
+          for (int i = 0; i < 16; ++i) prev[i] = 0.0;
+          if (a.emode == 2) {
+            const double2* pp = reinterpret_cast<const double2*>(O + r * TB + ch * 16);
+#pragma unroll
+            for (int i = 0; i < 8; ++i) {
+              const double2 t2 = pp[i];
+              prev[2 * i] = t2.x;
+              prev[2 * i + 1] = t2.y;
+            }
+          }
           double out[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) {
@@ -1073,7 +1098,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             const double fxd = inside ? (double)fx[i] : 0.0;
             const double z = inside ? zv[i] : 0.0;
             const bool dg = inside && gi == gj;
-            const double S = int_times_pow2(fxd, lsu);       // fx * su
+            const double S0 = int_times_pow2(fxd, lsu);      // fx * su
+            if (a.emode == 1) { out[i] = S0; continue; }     // finer groups only: S is stored
+            const double S = a.emode == 2 ? S0 + prev[i] : S0;
             double xn;
             // c2 S = (c2 su) fx exactly (su is a power of two)
             if (form == 1) xn = S;
@@ -1089,6 +1116,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) op[i] = make_double2(out[2 * i], out[2 * i + 1]);
         }
+        if (a.emode == 1) continue;
         // warp reductions (the tile's 32 rows are this warp's 32 lanes)
         for (int o = 16; o > 0; o >>= 1) {
           e2 += __shfl_xor_sync(FULLW, e2, o);
@@ -1135,6 +1163,7 @@ cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32
   ++g_launches;
   if (k == 2) k_panel_slices<2><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
   else if (k == 3) k_panel_slices<3><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
+  else if (k == 5) k_panel_slices<5><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
   else k_panel_slices<4><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
   return cudaGetLastError();
 }
@@ -1255,6 +1284,9 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   a.selftest = L.selftest ? 1 : 0;
   a.general = L.general ? 1 : 0;
   a.split_supply = L.split_supply ? 1 : 0;
+  a.glo = L.glo;
+  a.ghi = L.ghi < 0 ? L.k - 1 : L.ghi;
+  a.emode = L.emode;
   cudaError_t e = cudaSuccess;
   switch (L.k) {
     case 2:
@@ -1264,6 +1296,10 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
     case 3:
       e = cudaFuncSetAttribute(k_square_tc<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<3>::SMEM);
       if (e == cudaSuccess) { ++g_launches; k_square_tc<3><<<(unsigned)L.nsuper, TC_THREADS, TcCfg<3>::SMEM, st>>>(a); }
+      break;
+    case 5:
+      e = cudaFuncSetAttribute(k_square_tc<5>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<5>::SMEM);
+      if (e == cudaSuccess) { ++g_launches; k_square_tc<5><<<(unsigned)L.nsuper, TC_THREADS, TcCfg<5>::SMEM, st>>>(a); }
       break;
     default:
       e = cudaFuncSetAttribute(k_square_tc<4>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcCfg<4>::SMEM);

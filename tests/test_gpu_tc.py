@@ -154,3 +154,21 @@ def test_split_supply_gives_the_same_result(key, extra):
     assert a["stats"]["n"] == b["stats"]["n"]
     assert np.array_equal(a["brow"], b["brow"]) and np.array_equal(a["val"], b["val"])
     assert a["stats"]["e"] == b["stats"]["e"]
+
+
+@pytest.mark.parametrize("key", [1, "5s", "2s", "4s"])
+def test_split16_five_slices_fp64_grade_without_fp64_squares(key):
+    # five FP16 slices (finest grid 2^-54) in two launches per square: every
+    # square on the tensor cores (fp64_tail = 0), D at FP64 grade against the
+    # oracle, and the dense idempotency stop (1e-12) reached on tensor cores
+    c = make_config(key)
+    kw = dict(stop=c["stop"])
+    o = run_oracle(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], **kw)
+    g = run_gpu(c["F"], c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], precision="split16", slices=5,
+                fp64_tail=0.0, **kw)
+    err = _err(g, o)
+    print(f"config {key}: split16 k=5 ||D-Dref||_F = {err:.3e}, n = {g['stats']['n']} (oracle {o.n})")
+    assert g["code"] == 0 and g["stats"]["converged"]
+    assert all(p == 1 for p in g["stats"]["prec_hist"])
+    assert err <= 1e-9
+    assert abs(g["stats"]["n"] - o.n) <= 1
