@@ -752,7 +752,7 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   L.nsr = nsr;
   L.k = k;
   L.words = c->words;
-  c->ensure(c->tcscratch, (size_t)nsuper * 2 * 128 * 128 * 8);
+  c->ensure(c->tcscratch, (size_t)nsuper * tc_tile_slots() * 128 * 128 * 8);
   L.scratch = c->tcscratch.p;
   L.seg_min = c->prm.acc_flush_min;
   L.wait_ns = (unsigned long long)c->prm.wait_limit_ms * 1000000ull;

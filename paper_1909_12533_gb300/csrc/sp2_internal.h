@@ -179,7 +179,7 @@ struct TcLaunch {
   int64_t n;
   int nb, nsr, k, words;
   int32_t* err;
-  void* scratch;             // nsuper * 2 * 128 * 128 int64 (epilogue staging, two tiles per CTA)
+  void* scratch;             // nsuper * tc_tile_slots() * 128 * 128 int64 (epilogue staging per CTA)
   int seg_min;               // K loops of at least this many steps are accumulated in 16-step segments (0: never)
   unsigned long long wait_ns = 2000000000ull;   // limit of every bounded wait in the kernel
   bool selftest = false;     // wait first on a barrier nothing arrives at (tests the timeout path)
@@ -189,6 +189,7 @@ struct TcLaunch {
   int emode = 0;             // 0 full epilogue, 1 store S only, 2 full epilogue on S + the stored S
 };
 size_t panel_record_bytes(int k);
+int tc_tile_slots();   // tiles in flight between the producer and the epilogue of k_square_tc
 // report_range: also report an out-of-range element (error bit 4) without one
 // being present (self-test of the error path)
 cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32_t* slot, const double* pool,

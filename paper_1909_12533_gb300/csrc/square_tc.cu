@@ -285,9 +285,14 @@ __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ 
         if (x < 0) v = -v;
       } else if (ex != 0) {
         const unsigned long long m = ((unsigned long long)x & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
-        const int sh = 1075 + lscale - FIN - ex;   // >= 9 here
+        // sh >= 9 for four slices; with five (FIN = 54) values |x / scale| >= 1/4
+        // give sh <= 0, where the fixed-point value is m shifted left, exactly
+        // (|v| < 2^55 since |x / scale| < 2)
+        const int sh = 1075 + lscale - FIN - ex;
         unsigned long long qv = 0;
-        if (sh < 64) {
+        if (sh <= 0) {
+          qv = m << (-sh);
+        } else if (sh < 64) {
           qv = m >> sh;
           const unsigned long long rem = m & ((1ull << sh) - 1ull), half = 1ull << (sh - 1);
           if (rem > half || (rem == half && (qv & 1ull))) ++qv;
@@ -421,7 +426,7 @@ struct TcArgs {
   int64_t n;
   int nb, words, nsr;
   int32_t* err;
-  long long* scratch;       // per CTA, 2 slots: 128 x 128 fixed-point sums of a tile in its epilogue
+  long long* scratch;       // per CTA, NSLOT slots: 128 x 128 fixed-point sums of a tile in its epilogue
   int seg_min;              // K loops of at least this many steps are cut into 16-step segments (0: never)
   unsigned long long wait_ns;   // limit of every bounded wait
   int selftest;             // 1: the producer first waits on a barrier nothing arrives at (timeout path test)
@@ -454,6 +459,7 @@ constexpr uint32_t REC_LAST = 1u << 17;   // no more super-tiles (no data)
 constexpr uint32_t REC_SEG = 1u << 18;    // end of an accumulation segment of the super-tile (no data)
 constexpr uint32_t SEG_LAST = 1u << 31;   // segment record flag: last segment of its super-tile
 constexpr int SEG_RING = 4;               // accumulation segments in flight between MMA and epilogue
+constexpr int NSLOT = 3;                  // tiles in flight between the producer and the epilogue
 constexpr int SEG_KSTEPS = 16;            // K steps per accumulation segment of a segmented tile
 
 // record header byte: first nonzero slice (bits 0-2), tiles present (bits 4-7)
@@ -475,17 +481,17 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + STAGES * STAGE_BYTES);
   uint64_t* empty = full + STAGES;
   uint64_t* acc_full = empty + STAGES;     // [SEG_RING] MMAs of a segment done (commit) + its record written
-  uint64_t* tile_full = acc_full + SEG_RING;   // [2] tile slot written by the producer
-  uint64_t* tile_empty = tile_full + 2;    // [2] epilogue done with the tile slot (one arrive per warp)
-  uint64_t* drain = tile_empty + 2;        // MMAs issued before the exit are complete
+  uint64_t* tile_full = acc_full + SEG_RING;   // [NSLOT] tile slot written by the producer
+  uint64_t* tile_empty = tile_full + NSLOT;    // [NSLOT] epilogue done with the tile slot (one arrive per warp)
+  uint64_t* drain = tile_empty + NSLOT;    // MMAs issued before the exit are complete
   uint64_t* tmem_empty = drain + 1;        // [SEG_RING] every epilogue warp has read the segment's TMEM
   uint64_t* probe = tmem_empty + SEG_RING; // self-test: a barrier that nothing arrives at
   uint64_t* fill = probe + 1;              // [STAGES] stage record written: the copy warps may fill B
   const __half** srcb = reinterpret_cast<const __half**>(fill + STAGES);   // [STAGES] B record of the stage
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(srcb + STAGES);
-  int32_t* tslot = reinterpret_cast<int32_t*>(tmem_slot + 2);      // [2] super-tile list index, -1: none
-  int32_t* kcount = tslot + 2;                                      // [2][16] triplets per output tile
-  uint32_t* gmap = reinterpret_cast<uint32_t*>(kcount + 32);       // [SEG_RING] groups written, block of each, last flag
+  int32_t* tslot = reinterpret_cast<int32_t*>(tmem_slot + 2);      // [NSLOT] super-tile list index, -1: none
+  int32_t* kcount = tslot + NSLOT;                                  // [NSLOT][16] triplets per output tile
+  uint32_t* gmap = reinterpret_cast<uint32_t*>(kcount + 16 * NSLOT);   // [SEG_RING] groups written, block of each, last flag
   uint32_t* rec = gmap + SEG_RING;                                  // [STAGES] sub-step records
   int32_t* status = reinterpret_cast<int32_t*>(rec + STAGES);      // [0] a wait timed out
   uint4* ulist = reinterpret_cast<uint4*>(smem_raw + STAGES * STAGE_BYTES + 1024);   // [128] sub-steps of a batch
@@ -502,7 +508,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       mbar_init(&acc_full[b], 2);
       mbar_init(&tmem_empty[b], EPI_WARPS);
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < NSLOT; ++b) {
       mbar_init(&tile_full[b], 1);
       mbar_init(&tile_empty[b], EPI_WARPS);
     }
@@ -526,8 +532,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   // Persistent and warp-specialised: the producer (warp 0) takes super-tiles
   // from the work counter and streams their operand slices; the MMA issuer
   // (warp 1) accumulates each tile in TMEM blocks of 128 columns taken on
-  // first use; the epilogue (warps 4-7) finishes tile i while tiles i + 1 and
-  // i + 2 are being loaded and multiplied.  Tiles pass through two slots.
+  // first use; the epilogue (warps 2-9) finishes tile i while tiles i + 1 and
+  // i + 2 are being loaded and multiplied.  Tiles pass through NSLOT slots.
   if (warp == 0) {
     // ---------------- producer warp.  The record headers of 32 K steps are
     // fetched at a time (lane j: step j), one batch ahead of their use; the
@@ -593,10 +599,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       __syncwarp();
     }
     for (int it = 0; ok; ++it) {
-      const int b = it & 1;
-      // the slot's previous tile (it - 2) has left the epilogue
+      const int b = it % NSLOT;
+      // the slot's previous tile (it - NSLOT) has left the epilogue
       int good = 1;
-      if (lane == 0) good = mbar_wait_sleep(&tile_empty[b], (((uint32_t)it >> 1) & 1u) ^ 1u) ? 1 : 0;
+      if (lane == 0) good = mbar_wait_sleep(&tile_empty[b], (((uint32_t)(it / NSLOT)) & 1u) ^ 1u) ? 1 : 0;
       good = __shfl_sync(FULLW, good, 0);
       if (!good) {
         if (lane == 0) { status[0] = 1; note_timeout(a.err, 2); }
@@ -958,8 +964,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
     int seg = 0;   // segments consumed
     const uint64_t pol = policy_evict_last();
     for (int it = 0;; ++it) {
-      const int b = it & 1;
-      const uint32_t par = ((uint32_t)it >> 1) & 1u;
+      const int b = it % NSLOT;
+      const uint32_t par = ((uint32_t)(it / NSLOT)) & 1u;
       bool good = true;
       if (lane == 0) good = mbar_wait_sleep(&tile_full[b], par);
       good = __shfl_sync(FULLW, good ? 1 : 0, 0) != 0;
@@ -972,7 +978,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       const int I0 = 4 * R, J0 = 4 * C;
       const int Ia = I0 + quarter;           // tile row of this thread
       const int64_t gi = (int64_t)Ia * TB + r;
-      long long* scr = a.scratch + ((int64_t)blockIdx.x * 2 + b) * (ST * ST) + (int64_t)(quarter * 32 + r) * ST;
+      long long* scr = a.scratch + ((int64_t)blockIdx.x * NSLOT + b) * (ST * ST) + (int64_t)(quarter * 32 + r) * ST;
       // output tile index of each column tile
       int oidx[2];
 #pragma unroll
@@ -1310,4 +1316,8 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   return cudaGetLastError();
 }
 
+}  // namespace sp2
+
+namespace sp2 {
+int tc_tile_slots() { return NSLOT; }
 }  // namespace sp2
