@@ -213,6 +213,9 @@ def main(argv=None) -> int:
     ap.add_argument("--fp64-tail", type=float, default=None,
                     help="tensor path with the idempotency stop: FP64 squares once e_j < this (0: none); "
                          "default: library")
+    ap.add_argument("--trunc", default=None, choices=["frobenius", "frobinf", "mixed"],
+                    help="truncation norm (default: the library's, Frobenius)")
+    ap.add_argument("--part", type=int, default=None, help="Frob-Inf / mixed-norm partition in rows")
     ap.add_argument("--storage", default="symmetric", choices=["symmetric", "general"],
                     help="general: both triangles stored and computed (the paper's general-matrix form)")
     ap.add_argument("--no-fp64-compare", action="store_true", help="skip the timed FP64 reference run")
@@ -249,6 +252,10 @@ def main(argv=None) -> int:
     extra = {} if args.split_supply is None else {"split_supply": args.split_supply}
     if args.fp64_tail is not None:
         extra["fp64_tail"] = args.fp64_tail
+    if args.trunc is not None:
+        extra["trunc"] = args.trunc
+    if args.part is not None:
+        extra["frobinf_part"] = args.part
 
     def step(F, precision, keep_D=False):
         ctx = sp2.SP2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision=precision,
@@ -382,6 +389,7 @@ def main(argv=None) -> int:
         "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "f16x%d-split+f64" % args.slices,
         "data": "synthetic",
         "config": {"workload": wl["desc"], "precision": args.precision, "storage": args.storage,
+                   "trunc": args.trunc or "frobenius", "part": args.part,
                    "slices": args.slices if args.precision == "split16" else None,
                    "l2": "inputs larger than L2 (F alone is %.0f MB)" % (Fh.val.nbytes / 1e6),
                    "parallelism": "replicas" if world > 1 else "single GPU"},

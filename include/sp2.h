@@ -80,12 +80,14 @@ enum sp2_trunc     { SP2_TRUNC_FROBENIUS = 0, SP2_TRUNC_FROBINF = 1, SP2_TRUNC_M
  *            grids (slice s on the grid 2^-(11 s - 1)); products of slice pairs
  *            (s, t) with s + t <= slices + 1 accumulate exactly-grouped in FP32
  *            tensor memory and are combined in FP64.  slices = 2 is the
- *            hi+lo three-product form; slices = 5 (finest grid 2^-54,
- *            FP64-grade) runs each square as two launches: the finest group
- *            (s + t = 6) first, its exact sum left in the output tiles, then
- *            the other four groups added to it in the full epilogue (tensor
- *            memory holds four group accumulators); it does not record masks
- *            for sp2_backward.
+ *            hi+lo three-product form.  slices = 5 uses 10-bit slices
+ *            (finest grid 2^-49, FP64 grade for |x| <= 1) and runs each square
+ *            as two launches: the finest group (s + t = 6) first, its exact
+ *            sum left in the output tiles, then the other four groups added
+ *            to it in the full epilogue (tensor memory holds four group
+ *            accumulators), every K loop in segments of 8 K tiles; it does
+ *            not record masks for sp2_backward.  In every slice count the
+ *            diagonal of S (the squared row norms of X~) is taken in FP64.
  * Everything else (traces, norms, polynomial choice, stop test, truncation)
  * is FP64 in every precision. */
 enum sp2_precision { SP2_PREC_FP64 = 0, SP2_PREC_SPLIT16 = 1 };

@@ -357,7 +357,7 @@ struct sp2_ctx {
   std::vector<Rec> recs;
   std::vector<Buf> seg;
   Buf ident, fpB_bits, fpB_rowptr, fpB_col, fpB_ref, gpool[2], w_brow, w_bcol, w_rowptr, w_pool, dF;
-  Buf amax, trbuf;
+  Buf amax, trbuf, dsq;
   Buf gflag, gpos, gkeep, u_brow, u_bcol, u_slot;   // general storage: upper sub-index
   FullPattern fpB;
   double backward_ms = 0.0;
@@ -381,7 +381,7 @@ struct sp2_ctx {
                   &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &opx.sbits,
                   &opx.cnt, &opx.spos, &opx.index, &opx.head, &opx.data, &opy.sbits, &opy.cnt, &opy.spos,
                   &opy.index, &opy.head, &opy.data, &sflag, &spos, &slist, &errflag, &scount, &tcscratch, &redwork, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
-                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax, &trbuf, &gflag, &gpos, &gkeep,
+                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax, &trbuf, &dsq, &gflag, &gpos, &gkeep,
                   &u_brow, &u_bcol, &u_slot};
     for (Buf* b : all) bufs.push_back(b);
   }
@@ -763,7 +763,12 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
   if (c->prm.slices == 5 && !L.two_pass) {
     // five slices: the finest group (s + t = 4) first, its exact sum left in
     // the output tiles; then groups 0-3, added to it in the full epilogue
-    // (TMEM holds four group accumulators at a time)
+    // (TMEM holds four group accumulators at a time).  Every K loop is
+    // accumulated in segments of 8 K tiles: 256 products of up to 2^22 per
+    // element and group keep the FP32 group sums exact for dense operands,
+    // which the finer grid needs to pay off.
+    L.seg_min = 1;
+    L.seg_ksteps = 8;
     c->ck(cudaEventRecord(c->evs0, c->st), "event");
     TcLaunch Lf = L;
     Lf.glo = 4; Lf.ghi = 4; Lf.emode = 1;
@@ -787,6 +792,11 @@ void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool, boo
   // general storage: B is read by columns, from its own records
   L.Q = general ? prepare_operand(c, c->X, c->pool[c->cur].as<double>(), c->fpB, c->opy, 1.0) : L.P;
   L.general = general;
+  // the diagonal of S = X~^2 from the FP64 squared row norms of X~
+  c->ensure(c->dsq, (size_t)c->n * 8);
+  c->ck(launch_row_sq(c->fp, c->X.slot, c->pool[c->cur].as<double>(), c->nb, c->n, c->dsq.as<double>(), c->st),
+        "row norms");
+  L.dsq = c->dsq.as<double>();
   L.two_pass = false;
   L.scale = 1.0;
   L.Z = &c->fp;

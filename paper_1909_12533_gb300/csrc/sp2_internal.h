@@ -180,15 +180,20 @@ struct TcLaunch {
   int nb, nsr, k, words;
   int32_t* err;
   void* scratch;             // nsuper * tc_tile_slots() * 128 * 128 int64 (epilogue staging per CTA)
-  int seg_min;               // K loops of at least this many steps are accumulated in 16-step segments (0: never)
+  int seg_min;               // K loops of at least this many steps are accumulated in segments (0: never)
+  int seg_ksteps = 16;       // K steps per segment (8 or 16)
   unsigned long long wait_ns = 2000000000ull;   // limit of every bounded wait in the kernel
   bool selftest = false;     // wait first on a barrier nothing arrives at (tests the timeout path)
   bool general = false;      // general storage: every output tile of the square, weight 1 in e^2
   bool split_supply = false; // B operand units through copy warps (cp.async) beside the bulk copies of A
+  const double* dsq = nullptr;   // S_ii per global row in FP64 (symmetric square: the squared row norms)
   int glo = 0, ghi = -1;     // slice-pair groups s + t of the launch (ghi < 0: all, k - 1; at most 4 groups)
   int emode = 0;             // 0 full epilogue, 1 store S only, 2 full epilogue on S + the stored S
 };
 size_t panel_record_bytes(int k);
+// dsq[i] = sum_k x_ik^2 over the stored tiles of the both-triangle pattern fp (refs index slot, or the pool)
+cudaError_t launch_row_sq(const FullPattern& fp, const int32_t* slot, const double* pool, int nb, int64_t n,
+                          double* dsq, cudaStream_t st);
 int tc_tile_slots();   // tiles in flight between the producer and the epilogue of k_square_tc
 // report_range: also report an out-of-range element (error bit 4) without one
 // being present (self-test of the error path)

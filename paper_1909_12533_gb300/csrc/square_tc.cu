@@ -5,6 +5,7 @@
 // every element x of X~ (|x| < 2 for an SP2 iterate, whose eigenvalues stay in
 // about [0, 1]) is written on fixed absolute grids,
 //     x ~= sum_{s=1..k} T_s * 2^-(11 s - 1),   T_s integers, |T_s| <= 2048,
+// (11-bit slices; five slices use 10-bit ones, see slice_bits)
 // so each slice T_s is exact in FP16.  The product of slices s and t has the
 // unit 2^-(11 (s + t) - 2); all pairs with the same g = s + t share one FP32
 // accumulator in tensor memory.  Their sums are integers: the g = 2 group
@@ -51,6 +52,11 @@ namespace sp2 {
 namespace {
 
 constexpr int ST = 128;          // super-tile edge (4 tiles)
+
+// Bits per slice: 11 (FP16 holds integers up to 2^11 exactly) for two to four
+// slices; 10 for five, whose smaller digits keep the FP32 group sums of dense
+// rows exact with room to spare (finest grid 2^-49, FP64 grade for |x| <= 1).
+__host__ __device__ constexpr int slice_bits(int k) { return k == 5 ? 10 : 11; }
 constexpr int SLICE_BYTES = 2048;  // one 32 x 32 FP16 slice
 
 // ------------------------------------------------------------------ PTX helpers
@@ -105,7 +111,8 @@ __device__ __forceinline__ bool mbar_try_wait_sleep(uint64_t* bar, uint32_t pari
 }
 
 // Timeout sites of a launch, for the error message (err[1], bit 0 self-test
-// probe, 8 copy warps, 1 producer stage, 2 producer tile slot, 3 MMA data, 4 MMA TMEM or segment slot, 5 MMA
+// probe, 8 copy warps, 9 copies still in flight at an error exit, 1 producer
+// stage, 2 producer tile slot, 3 MMA data, 4 MMA TMEM or segment slot, 5 MMA
 // drain, 6 epilogue tile, 7 epilogue segment).
 __device__ __forceinline__ void note_timeout(int32_t* err, int where) {
   if (err) atomicOr(err + 1, 1 << where);
@@ -252,7 +259,8 @@ __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ 
   if (report_range && e == 0 && threadIdx.x == 0 && err) atomicOr(err, 4);
   const uint4 iw = index[e];
   const uint32_t wd[4] = {iw.x, iw.y, iw.z, iw.w};
-  constexpr int FIN = 11 * K - 1;                  // finest grid 2^-FIN
+  constexpr int W = slice_bits(K);
+  constexpr int FIN = W * K - 1;                   // finest grid 2^-FIN
   constexpr int PER = TE / 256;                    // elements of a tile per thread
   // all loads first (16 per thread), then the integer work
   long long xb[4][PER];
@@ -285,9 +293,8 @@ __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ 
         if (x < 0) v = -v;
       } else if (ex != 0) {
         const unsigned long long m = ((unsigned long long)x & 0x000FFFFFFFFFFFFFull) | (1ull << 52);
-        // sh >= 9 for four slices; with five (FIN = 54) values |x / scale| >= 1/4
-        // give sh <= 0, where the fixed-point value is m shifted left, exactly
-        // (|v| < 2^55 since |x / scale| < 2)
+        // sh >= 3 for every slice count used (FIN <= 49); a left shift, exact
+        // (|v| < 2^(FIN + 1)), covers sh <= 0
         const int sh = 1075 + lscale - FIN - ex;
         unsigned long long qv = 0;
         if (sh <= 0) {
@@ -302,7 +309,7 @@ __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ 
       int T[K];
 #pragma unroll
       for (int s = 0; s < K - 1; ++s) {
-        const int sh = 11 * (K - 1 - s);
+        const int sh = W * (K - 1 - s);
         const long long hi = (v + (1ll << (sh - 1))) >> sh;   // round to nearest (ties up)
         T[s] = (int)hi;
         v -= hi * (1ll << sh);
@@ -330,6 +337,31 @@ __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ 
   const uint4* s4 = reinterpret_cast<const uint4*>(sm);
   uint4* d4 = reinterpret_cast<uint4*>(data + e * (int64_t)(K * 4 * TE));
   for (int i = first_s * (4 * TE / 8) + threadIdx.x; i < K * 4 * TE / 8; i += blockDim.x) d4[i] = s4[i];
+}
+
+// dsq[32 R + r] = sum over the stored tiles of tile row R (both triangles, as
+// the both-triangle pattern lists them) of the squares of row r: S_ii of
+// S = X~^2 for symmetric X~.  One warp per tile row, lane r for row r, tiles in
+// pattern order and columns in order (deterministic).
+__global__ void k_row_sq(const int32_t* __restrict__ rowptr, const uint32_t* __restrict__ ref,
+                         const int32_t* __restrict__ slot, const double* __restrict__ pool, int nb, int64_t n,
+                         double* dsq) {
+  const int R = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
+  const int r = threadIdx.x & 31;
+  if (R >= nb) return;
+  double acc = 0.0;
+  for (int p = rowptr[R]; p < rowptr[R + 1]; ++p) {
+    const uint32_t rf = ref[p];
+    const int64_t ti = (int64_t)(rf & ~REF_T);
+    const double* x = pool + (int64_t)(slot ? slot[ti] : ti) * TE;
+    if (rf & REF_T) {
+      for (int c = 0; c < TB; ++c) { const double v = x[c * TB + r]; acc = fma(v, v, acc); }
+    } else {
+      for (int c = 0; c < TB; ++c) { const double v = x[r * TB + c]; acc = fma(v, v, acc); }
+    }
+  }
+  const int64_t gi = (int64_t)R * TB + r;
+  if (gi < n) dsq[gi] = acc;
 }
 
 // super-row bitmap: OR of the 4 tile rows
@@ -427,11 +459,13 @@ struct TcArgs {
   int nb, words, nsr;
   int32_t* err;
   long long* scratch;       // per CTA, NSLOT slots: 128 x 128 fixed-point sums of a tile in its epilogue
-  int seg_min;              // K loops of at least this many steps are cut into 16-step segments (0: never)
+  int seg_min;              // K loops of at least this many steps are cut into segments (0: never)
+  int seg_ksteps;           // K steps per segment (8 or 16, divides the 32-step batch)
   unsigned long long wait_ns;   // limit of every bounded wait
   int selftest;             // 1: the producer first waits on a barrier nothing arrives at (timeout path test)
   int general;              // general storage: output tiles on both sides of the diagonal, weight 1 in e^2
   int split_supply;         // 1: the B units come through the copy warps (cp.async), the A units by bulk copy
+  const double* dsq;        // S_ii = sum_k x_ik^2 in FP64 per global row (nullptr: from the tensor cores)
   int glo, ghi;             // slice-pair groups s + t of this launch (ghi - glo <= 3)
   int emode;                // 0: full epilogue; 1: write S (this launch's groups) into the output tiles only;
                             // 2: full epilogue on S + the S already in the output tiles
@@ -459,8 +493,8 @@ constexpr uint32_t REC_LAST = 1u << 17;   // no more super-tiles (no data)
 constexpr uint32_t REC_SEG = 1u << 18;    // end of an accumulation segment of the super-tile (no data)
 constexpr uint32_t SEG_LAST = 1u << 31;   // segment record flag: last segment of its super-tile
 constexpr int SEG_RING = 4;               // accumulation segments in flight between MMA and epilogue
-constexpr int NSLOT = 3;                  // tiles in flight between the producer and the epilogue
-constexpr int SEG_KSTEPS = 16;            // K steps per accumulation segment of a segmented tile
+constexpr int NSLOT = 2;                  // tiles in flight between the producer and the epilogue (3 measured 13% slower)
+constexpr int SEG_KSTEPS = 16;            // K steps per accumulation segment of a segmented tile (default)
 
 // record header byte: first nonzero slice (bits 0-2), tiles present (bits 4-7)
 constexpr uint32_t HEAD_NONE = 0x07u;   // header of a K index outside the step list
@@ -468,8 +502,6 @@ constexpr uint32_t HEAD_NONE = 0x07u;   // header of a K index outside the step 
 template <int K>
 struct TcCfg {
   static constexpr int SMEM = STAGES * STAGE_BYTES + 1024 + 128 * 16;
-  // unit of the finest group, 2^-(11 (k + 1) - 2)
-  static constexpr double UNIT = 1.0 / (double)(1ull << (11 * (K + 1) - 2));
 };
 
 template <int K>
@@ -542,6 +574,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
     // lane 0 writing the stage record and arming its barrier.  Every lane keeps
     // its own copy of the stage counter; no warp votes per sub-step.
     int step = 0;
+    int emitted = 0;   // stages whose copies were issued (lane 0's view)
     bool ok = true;
     // lanes 0-3: one sub-step (srcA / srcB: the K step's A and B panel records).
     // Lane 0 waits for the stage and the others take its result, so the four
@@ -576,6 +609,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
                  (lane < 2 ? srcA : srcB) + (int64_t)((rv >> (3 * lane)) & 7u) * (UNIT_BYTES / 2), UNIT_BYTES,
                  &full[s]);
       if (a.split_supply && lane == 0) mbar_arrive(&fill[s]);   // release: record and B source visible
+      emitted = step;
       return true;
     };
     // all lanes: a control sub-step (no data) through lanes 0-3
@@ -732,8 +766,9 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
                 ++ns;
               }
             }
-            // a segmented tile also closes a segment before K steps 16 of the batch
-            const int lead = (segmented && lane == SEG_KSTEPS && jb + lane < total) ? 1 : 0;
+            // a segmented tile also closes a segment before every seg_ksteps-th K
+            // step inside the batch (the batch end closes one too)
+            const int lead = (segmented && lane > 0 && (lane % a.seg_ksteps) == 0 && jb + lane < total) ? 1 : 0;
             int soff = ns + lead;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
@@ -776,6 +811,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
       if (lane < 16) kcount[b * 16 + lane] = kc;
       __syncwarp();
       if (ok) ok = emit_ctl(REC_END);
+    }
+    // after a timeout anywhere in the CTA: wait (bounded) until the copies of
+    // the last STAGES emitted stages have landed, so that no bulk copy into
+    // this CTA's shared memory is in flight when the CTA exits
+    if (lane == 0 && *(volatile int32_t*)status != 0) {
+      for (int j = max(0, emitted - STAGES); j < emitted; ++j)
+        if (!mbar_wait(&full[j % STAGES], (uint32_t)(j / STAGES) & 1u)) note_timeout(a.err, 9);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer.  TMEM is four blocks of 128 columns; a group
@@ -940,9 +982,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
     const int quarter = warp & 3;
     const int bt0 = 2 * ((warp - 2) >> 2);
     const int r = lane;
-    // unit of the finest group of the window: slice s lies on the grid
-    // 2^-(11 s + 10), so group g = s + t has the unit 2^-(11 g + 20)
-    const double su = ldexp(1.0, -(11 * a.ghi + 20)) * a.scale;   // S = fx * su, su a power of two
+    // unit of the finest group of the window: with W bits per slice, slice s
+    // lies on the grid 2^-(W s + W - 1), so group g = s + t has the unit
+    // 2^-(W g + 2 W - 2)
+    constexpr int W = slice_bits(K);
+    const double su = ldexp(1.0, -(W * a.ghi + 2 * W - 2)) * a.scale;   // S = fx * su, su a power of two
     const int lsu = ilogb(su);
     // X_new = c0 I + c1 X~ + c2 S.  Without acceleration (alpha = 1) the two
     // polynomials need fewer FP64 operations, with the same results:
@@ -1029,7 +1073,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
                 const uint32_t blk = (gm >> (8 + 2 * gg)) & 3u;
                 tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + blk * ST + (uint32_t)col0, g);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) fx[i] += f32_int_to_ll(g[i]) * (1ll << (11 * (a.ghi - a.glo - gg)));
+                for (int i = 0; i < 16; ++i) fx[i] += f32_int_to_ll(g[i]) * (1ll << (W * (a.ghi - a.glo - gg)));
               }
             }
 #pragma unroll
@@ -1106,7 +1150,10 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             const bool dg = inside && gi == gj;
             const double S0 = int_times_pow2(fxd, lsu);      // fx * su
             if (a.emode == 1) { out[i] = S0; continue; }     // finer groups only: S is stored
-            const double S = a.emode == 2 ? S0 + prev[i] : S0;
+            // the diagonal of S = X~^2 is the squared row norm, taken in FP64
+            // (its digit products are all positive and pass the exact range
+            // of the FP32 group sums on dense rows)
+            const double S = (dg && a.dsq) ? a.dsq[gi] : (a.emode == 2 ? S0 + prev[i] : S0);
             double xn;
             // c2 S = (c2 su) fx exactly (su is a power of two)
             if (form == 1) xn = S;
@@ -1199,6 +1246,14 @@ __global__ void k_panel_fill(const int32_t* __restrict__ frowptr, const int32_t*
   }
 }
 
+cudaError_t launch_row_sq(const FullPattern& fp, const int32_t* slot, const double* pool, int nb, int64_t n,
+                          double* dsq, cudaStream_t st) {
+  if (nb == 0) return cudaSuccess;
+  ++g_launches;
+  k_row_sq<<<grid_for((int64_t)nb * 32, 256), 256, 0, st>>>(fp.rowptr, fp.ref, slot, pool, nb, n, dsq);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_popc_words(const uint32_t* bits, int64_t n, int32_t* cnt, cudaStream_t st) {
   if (n == 0) return cudaSuccess;
   ++g_launches;
@@ -1286,10 +1341,12 @@ cudaError_t launch_square_tc(const TcLaunch& L, cudaStream_t st) {
   a.part = L.part; a.c0 = L.c0; a.c1 = L.c1; a.c2 = L.c2; a.scale = L.scale; a.n = L.n; a.nb = L.nb;
   a.words = L.words; a.nsr = L.nsr; a.err = L.err; a.scratch = static_cast<long long*>(L.scratch);
   a.seg_min = L.seg_min;
+  a.seg_ksteps = L.seg_ksteps > 0 ? L.seg_ksteps : SEG_KSTEPS;
   a.wait_ns = L.wait_ns;
   a.selftest = L.selftest ? 1 : 0;
   a.general = L.general ? 1 : 0;
   a.split_supply = L.split_supply ? 1 : 0;
+  a.dsq = L.dsq;
   a.glo = L.glo;
   a.ghi = L.ghi < 0 ? L.k - 1 : L.ghi;
   a.emode = L.emode;

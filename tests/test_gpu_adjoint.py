@@ -208,3 +208,32 @@ def test_adjoint_split16_central_finite_differences():
         fd = (Lp - Lm) / (2 * h)
         an = G[i, j] + (G[j, i] if i != j else 0.0)
         assert abs(fd - an) <= 1e-5 * max(1.0, abs(an)), (i, j, fd, an)
+
+
+def test_autograd_function_second_backward_and_not_converged():
+    # the context stays open until the autograd node is freed: a second
+    # backward (retain_graph) runs the same recorded sweep; a forward that ends
+    # at n_max without the stop test raises unless allow_not_converged is set
+    import torch
+    import paper_1909_12533_gb300 as sp2
+    n, nocc = 70, 30
+    d = dense_gapped(n, nocc, (-1.5, -0.4), (0.4, 1.5), seed=13)
+    Fb = from_dense(d["F"])
+    Fv = torch.from_numpy(Fb.val).cuda().requires_grad_(True)
+    br = torch.from_numpy(Fb.brow).cuda()
+    bc = torch.from_numpy(Fb.bcol).cuda()
+    Fn = sp2.SP2Function
+    Dv, _, _ = Fn.apply(Fv, br, bc, n, nocc, d["homo_ub"], d["lumo_lb"], 0.0, {"stop": "idempotency"})
+    R = torch.randn(Dv.shape, dtype=torch.float64, device="cuda", generator=torch.Generator("cuda").manual_seed(2))
+    L = (Dv * R).sum()
+    L.backward(retain_graph=True)
+    g1 = Fv.grad.clone()
+    Fv.grad = None
+    L.backward()
+    assert torch.equal(Fv.grad, g1)
+    with pytest.raises(sp2.SP2Error) as e:
+        Fn.apply(Fv, br, bc, n, nocc, d["homo_ub"], d["lumo_lb"], 0.0, {"stop": "idempotency", "n_max_cap": 3})
+    assert e.value.code == -7
+    Dv3, _, _ = Fn.apply(Fv, br, bc, n, nocc, d["homo_ub"], d["lumo_lb"], 0.0,
+                         {"stop": "idempotency", "n_max_cap": 3, "allow_not_converged": True})
+    assert torch.isfinite(Dv3).all()
