@@ -357,7 +357,7 @@ struct sp2_ctx {
   std::vector<Rec> recs;
   std::vector<Buf> seg;
   Buf ident, fpB_bits, fpB_rowptr, fpB_col, fpB_ref, gpool[2], w_brow, w_bcol, w_rowptr, w_pool, dF;
-  Buf amax, trbuf, dsq;
+  Buf amax, trbuf, dsq, rsq;
   Buf gflag, gpos, gkeep, u_brow, u_bcol, u_slot;   // general storage: upper sub-index
   FullPattern fpB;
   double backward_ms = 0.0;
@@ -381,7 +381,7 @@ struct sp2_ctx {
                   &twork, &rowlo, &rowhi, &dsc, &dcnt, &d2, &d_brow, &d_bcol, &d_val, &opx.sbits,
                   &opx.cnt, &opx.spos, &opx.index, &opx.head, &opx.data, &opy.sbits, &opy.cnt, &opy.spos,
                   &opy.index, &opy.head, &opy.data, &sflag, &spos, &slist, &errflag, &scount, &tcscratch, &redwork, &ident, &fpB_bits, &fpB_rowptr, &fpB_col,
-                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax, &trbuf, &dsq, &gflag, &gpos, &gkeep,
+                  &fpB_ref, &gpool[0], &gpool[1], &w_brow, &w_bcol, &w_rowptr, &w_pool, &dF, &amax, &trbuf, &dsq, &rsq, &gflag, &gpos, &gkeep,
                   &u_brow, &u_bcol, &u_slot};
     for (Buf* b : all) bufs.push_back(b);
   }
@@ -666,9 +666,10 @@ bool use_tc(const sp2_ctx* c, int i) {
 // Panel records of the tiles of `x` (values at pool slot x.slot[t] of tile
 // index t) on its both-triangle pattern `fp`: super-row bitmaps, record
 // offsets, record index words, then the FP16 slices and header of every
-// record.  Reads the number of records back (one host round trip).
+// record.  Reads the number of records back (one host round trip).  With
+// dsq: also the squared row norms of x into dsq (n doubles; FP64, unscaled).
 TcOp prepare_operand(sp2_ctx* c, const TileSet& x, const double* pool, const FullPattern& fp, OpBufs& ob,
-                     double scale) {
+                     double scale, double* dsq = nullptr) {
   const int k = c->prm.slices;
   const int nsr = (c->nb + 3) / 4;
   const int64_t nw = (int64_t)nsr * c->words;
@@ -691,10 +692,17 @@ TcOp prepare_operand(sp2_ctx* c, const TileSet& x, const double* pool, const Ful
     c->ck(launch_panel_fill(fp, c->nb, ob.sbits.as<uint32_t>(), ob.spos.as<int32_t>(), ob.index.as<uint32_t>(),
                             c->st),
           "record index");
+    if (dsq) c->ensure(c->rsq, nr * 128 * 8);
     c->ck(launch_panel_slices(ob.index.as<uint32_t>(), nrec, x.slot, pool, ob.data.p, ob.head.as<uint8_t>(), k,
-                              c->errflag.as<int32_t>(), scale, c->selftest_pending == 2, c->st),
+                              c->errflag.as<int32_t>(), dsq ? c->rsq.as<double>() : nullptr, scale,
+                              c->selftest_pending == 2, c->st),
           "record slices");
     if (c->selftest_pending == 2) c->selftest_pending = 0;
+    if (dsq)
+      c->ck(launch_row_sq_sum(ob.spos.as<int32_t>(), nsr, c->words, c->rsq.as<double>(), c->n, dsq, c->st),
+            "row norms");
+  } else if (dsq) {
+    c->ck(cudaMemsetAsync(dsq, 0, (size_t)c->n * 8, c->st), "memset");
   }
   TcOp op;
   op.sbits = ob.sbits.as<uint32_t>();
@@ -788,14 +796,13 @@ void run_tc(sp2_ctx* c, TcLaunch& L, const uint32_t* obits, const int32_t* orowp
 // Forward: S = X~^2 on the product pattern (o_bits, upper only) with the fused epilogue.
 void square_tc(sp2_ctx* c, double c0, double c1, double c2, double* outpool, bool general) {
   TcLaunch L{};
-  L.P = prepare_operand(c, c->X, c->pool[c->cur].as<double>(), c->fp, c->opx, 1.0);
+  // the diagonal of S = X~^2 from the FP64 squared row norms of X~, summed
+  // while the records of A are sliced
+  c->ensure(c->dsq, (size_t)c->n * 8);
+  L.P = prepare_operand(c, c->X, c->pool[c->cur].as<double>(), c->fp, c->opx, 1.0, c->dsq.as<double>());
   // general storage: B is read by columns, from its own records
   L.Q = general ? prepare_operand(c, c->X, c->pool[c->cur].as<double>(), c->fpB, c->opy, 1.0) : L.P;
   L.general = general;
-  // the diagonal of S = X~^2 from the FP64 squared row norms of X~
-  c->ensure(c->dsq, (size_t)c->n * 8);
-  c->ck(launch_row_sq(c->fp, c->X.slot, c->pool[c->cur].as<double>(), c->nb, c->n, c->dsq.as<double>(), c->st),
-        "row norms");
   L.dsq = c->dsq.as<double>();
   L.two_pass = false;
   L.scale = 1.0;

@@ -191,15 +191,17 @@ struct TcLaunch {
   int emode = 0;             // 0 full epilogue, 1 store S only, 2 full epilogue on S + the stored S
 };
 size_t panel_record_bytes(int k);
-// dsq[i] = sum_k x_ik^2 over the stored tiles of the both-triangle pattern fp (refs index slot, or the pool)
-cudaError_t launch_row_sq(const FullPattern& fp, const int32_t* slot, const double* pool, int nb, int64_t n,
-                          double* dsq, cudaStream_t st);
+// dsq[i] = sum_k x_ik^2 from the per-record squared row sums rsq of an
+// operand's panel records (spos: the operand's record offsets, nsr x words + 1)
+cudaError_t launch_row_sq_sum(const int32_t* spos, int nsr, int words, const double* rsq, int64_t n, double* dsq,
+                              cudaStream_t st);
 int tc_tile_slots();   // tiles in flight between the producer and the epilogue of k_square_tc
 // report_range: also report an out-of-range element (error bit 4) without one
-// being present (self-test of the error path)
+// being present (self-test of the error path); rsq (nullptr: skipped): 128
+// squared row sums per record, FP64, unscaled
 cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32_t* slot, const double* pool,
-                                void* data, uint8_t* head, int k, int32_t* err, double scale, bool report_range,
-                                cudaStream_t st);
+                                void* data, uint8_t* head, int k, int32_t* err, double* rsq, double scale,
+                                bool report_range, cudaStream_t st);
 cudaError_t launch_popc_words(const uint32_t* bits, int64_t n, int32_t* cnt, cudaStream_t st);
 cudaError_t launch_panel_fill(const FullPattern& fp, int nb, const uint32_t* sbits, const int32_t* spos,
                               uint32_t* index, cudaStream_t st);

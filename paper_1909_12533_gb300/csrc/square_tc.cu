@@ -188,6 +188,10 @@ __device__ __forceinline__ double int_times_pow2(double x, int k) {
   return (hi & 0x7FFFFFFF) == 0 ? x : __hiloint2double(hi + (k << 20), __double2loint(x));
 }
 
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 // 2 z exactly (an exponent increment for normal z; the FP64 add otherwise).
 __device__ __forceinline__ double twice(double z) {
   const int hi = __double2hiint(z);
@@ -248,10 +252,16 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
 // byte holds the first slice that is not all zero in any of the 4 tiles (k if
 // none) in bits 0-2 and the tiles present in bits 4-7; units below that slice
 // are all zero, are never read, and are not written.
+//
+// rsq (optional): rsq[128 e + 32 q + r] = sum_c x_rc^2 of row r of tile q in
+// FP64, unscaled (0 for an absent tile).  Summed over the records of a
+// super-row (k_row_sq_sum) they give the squared row norms of the matrix, the
+// diagonal of its square.
 template <int K>
-__global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ index, const int32_t* __restrict__ slot,
+__global__ void __launch_bounds__(256, 5) k_panel_slices(const uint4* __restrict__ index, const int32_t* __restrict__ slot,
                                                        const double* __restrict__ pool, __half* data,
-                                                       uint8_t* head, int32_t* err, int lscale, int report_range) {
+                                                       uint8_t* head, int32_t* err, double* rsq, int lscale,
+                                                       int report_range) {
   __shared__ __align__(16) __half sm[K * 4 * TE];
   __shared__ uint32_t wnz[8];
   __shared__ int first_s;
@@ -273,10 +283,40 @@ __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ 
   }
   uint32_t nz = 0;                                 // bit s: slice s has a nonzero element
   uint32_t pres = 0;
+  // Squared row sums (rsq): thread 32 w + l holds stored row w + 8 k, column
+  // l.  Row w + 8 k of a tile used as stored is complete in warp w (a sum over
+  // the lanes: lanes 8 k .. 8 k + 7 keep it in rs[q]); row l of a tile used
+  // transposed is spread over the 8 warps (rs[q] = the sum over k here, over
+  // the warps at the end).  Fixed order throughout (deterministic).
+  static_assert(PER == 4, "four elements of a tile per thread");
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  double rs[4];
 #pragma unroll
   for (int q = 0; q < 4; ++q) {
     pres |= (wd[q] != 0xFFFFFFFFu ? 1u : 0u) << q;
     const bool tr = (wd[q] & REF_T) != 0;
+    rs[q] = 0.0;
+    if (rsq) {
+      double v[PER];
+#pragma unroll
+      for (int k = 0; k < PER; ++k) {
+        const double x = __longlong_as_double(xb[q][k]);
+        v[k] = x * x;
+      }
+      if (tr) {
+        rs[q] = (v[0] + v[1]) + (v[2] + v[3]);
+      } else {
+        // reduce-scatter of the 4 rows over the lanes
+        const bool b16 = (lane & 16) != 0, b8 = (lane & 8) != 0;
+        const double h0 = (b16 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, b16 ? v[0] : v[2], 16);
+        const double h1 = (b16 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, b16 ? v[1] : v[3], 16);
+        double t = (b8 ? h1 : h0) + __shfl_xor_sync(0xffffffffu, b8 ? h0 : h1, 8);
+        t += __shfl_xor_sync(0xffffffffu, t, 4);
+        t += __shfl_xor_sync(0xffffffffu, t, 2);
+        t += __shfl_xor_sync(0xffffffffu, t, 1);
+        rs[q] = t;
+      }
+    }
 #pragma unroll
     for (int k = 0; k < PER; ++k) {
       const int i = threadIdx.x + 256 * k;
@@ -337,30 +377,48 @@ __global__ void __launch_bounds__(256) k_panel_slices(const uint4* __restrict__ 
   const uint4* s4 = reinterpret_cast<const uint4*>(sm);
   uint4* d4 = reinterpret_cast<uint4*>(data + e * (int64_t)(K * 4 * TE));
   for (int i = first_s * (4 * TE / 8) + threadIdx.x; i < K * 4 * TE / 8; i += blockDim.x) d4[i] = s4[i];
-}
-
-// dsq[32 R + r] = sum over the stored tiles of tile row R (both triangles, as
-// the both-triangle pattern lists them) of the squares of row r: S_ii of
-// S = X~^2 for symmetric X~.  One warp per tile row, lane r for row r, tiles in
-// pattern order and columns in order (deterministic).
-__global__ void k_row_sq(const int32_t* __restrict__ rowptr, const uint32_t* __restrict__ ref,
-                         const int32_t* __restrict__ slot, const double* __restrict__ pool, int nb, int64_t n,
-                         double* dsq) {
-  const int R = (int)((blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5);
-  const int r = threadIdx.x & 31;
-  if (R >= nb) return;
-  double acc = 0.0;
-  for (int p = rowptr[R]; p < rowptr[R + 1]; ++p) {
-    const uint32_t rf = ref[p];
-    const int64_t ti = (int64_t)(rf & ~REF_T);
-    const double* x = pool + (int64_t)(slot ? slot[ti] : ti) * TE;
-    if (rf & REF_T) {
-      for (int c = 0; c < TB; ++c) { const double v = x[c * TB + r]; acc = fma(v, v, acc); }
+  if (!rsq) return;
+  __syncthreads();                                 // sm is free: reused for the warp sums
+  double* red = reinterpret_cast<double*>(sm);     // [8 warps][4 tiles][32 rows]
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    if ((wd[q] & REF_T) != 0) {
+      red[wid * 128 + q * 32 + lane] = rs[q];
     } else {
-      for (int c = 0; c < TB; ++c) { const double v = x[r * TB + c]; acc = fma(v, v, acc); }
+      red[wid * 128 + q * 32 + lane] = 0.0;
+      __syncwarp();
+      if ((lane & 7) == 0) red[wid * 128 + q * 32 + wid + 8 * (lane >> 3)] = rs[q];
     }
   }
-  const int64_t gi = (int64_t)R * TB + r;
+  __syncthreads();
+  if (threadIdx.x < 128) {
+    double sum = 0.0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u) sum += red[u * 128 + threadIdx.x];
+    rsq[e * 128 + threadIdx.x] = sum;
+  }
+}
+
+// dsq[128 P + j] = sum of rsq[128 e + j] over the panel records e of
+// super-row P, in record order (the squared row norms; see k_panel_slices).
+// One CTA of 128 threads per super-row.
+__global__ void __launch_bounds__(128) k_row_sq_sum(const int32_t* __restrict__ spos, int words,
+                                                    const double* __restrict__ rsq, int64_t n, double* dsq) {
+  const int64_t P = blockIdx.x;
+  const int j = threadIdx.x;
+  const int64_t lo = spos[P * words], hi = spos[(P + 1) * words];
+  double acc = 0.0;
+  int64_t e = lo;
+  for (; e + 4 <= hi; e += 4) {
+    const double v0 = rsq[e * 128 + j], v1 = rsq[(e + 1) * 128 + j], v2 = rsq[(e + 2) * 128 + j],
+                 v3 = rsq[(e + 3) * 128 + j];
+    acc += v0;
+    acc += v1;
+    acc += v2;
+    acc += v3;
+  }
+  for (; e < hi; ++e) acc += rsq[e * 128 + j];
+  const int64_t gi = P * 128 + j;
   if (gi < n) dsq[gi] = acc;
 }
 
@@ -508,6 +566,9 @@ template <int K>
 __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
   using Cfg = TcCfg<K>;
   constexpr unsigned FULLW = 0xffffffffu;
+  // the group window and the epilogue mode vary only with five slices; fewer
+  // slices take every group in one launch (compile-time constants)
+  const int glo = K == 5 ? a.glo : 0, ghi = K == 5 ? a.ghi : K - 1, emode = K == 5 ? a.emode : 0;
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   unsigned char* stage_base = smem_raw;
   uint64_t* full = reinterpret_cast<uint64_t*>(smem_raw + STAGES * STAGE_BYTES);
@@ -748,13 +809,13 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             const int fa = (int)(ha & 7u), fb = (int)(hb & 7u);
             uint32_t rv0 = 0u, rv1 = 0u, rv2 = 0u;
             int ns = 0;
-            for (int a0 = fa; a0 <= K - 1 && a0 + fb <= a.ghi; a0 += 2) {
-              for (int b0 = max(fb, a.glo - a0 - 1); b0 <= K - 1 && a0 + b0 <= a.ghi; b0 += 2) {
+            for (int a0 = fa; a0 <= K - 1 && a0 + fb <= ghi; a0 += 2) {
+              for (int b0 = max(fb, glo - a0 - 1); b0 <= K - 1 && a0 + b0 <= ghi; b0 += 2) {
                 uint32_t mask = 0;
                 for (int i = 0; i < 2; ++i)
                   for (int jj = 0; jj < 2; ++jj) {
                     const int si = a0 + i, tj = b0 + jj;
-                    if (si <= K - 1 && tj <= K - 1 && si + tj >= a.glo && si + tj <= a.ghi)
+                    if (si <= K - 1 && tj <= K - 1 && si + tj >= glo && si + tj <= ghi)
                       mask |= 1u << (2 * i + jj);
                   }
                 if (!mask) continue;
@@ -878,7 +939,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           for (int j = 0; j < 2; ++j) {
             if (!((rv >> (12 + 2 * i + j)) & 1u)) continue;
             // group relative to the launch's window (at most four groups live)
-            const int g = (int)((rv >> (3 * i)) & 7u) + (int)((rv >> (6 + 3 * j)) & 7u) - a.glo;
+            const int g = (int)((rv >> (3 * i)) & 7u) + (int)((rv >> (6 + 3 * j)) & 7u) - glo;
             if (!((written >> g) & 1u)) {
               while (free_mask == 0u && ok) ok = reclaim();
               if (!ok) break;
@@ -986,7 +1047,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
     // lies on the grid 2^-(W s + W - 1), so group g = s + t has the unit
     // 2^-(W g + 2 W - 2)
     constexpr int W = slice_bits(K);
-    const double su = ldexp(1.0, -(W * a.ghi + 2 * W - 2)) * a.scale;   // S = fx * su, su a power of two
+    const double su = ldexp(1.0, -(W * ghi + 2 * W - 2)) * a.scale;   // S = fx * su, su a power of two
     const int lsu = ilogb(su);
     // X_new = c0 I + c1 X~ + c2 S.  Without acceleration (alpha = 1) the two
     // polynomials need fewer FP64 operations, with the same results:
@@ -1030,6 +1091,20 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
         const int Jb = J0 + bt0 + h;
         oidx[h] = (Ia < a.nb && Jb < a.nb && (a.general || Ia <= Jb)) ? find(a.obits, a.orowptr, Ia, Jb) : -1;
       }
+      // Z_IJ of each output tile (X~_IJ in the forward step; absent -> null),
+      // looked up and its row requested into L2 before the accumulators are
+      // waited for, so that the chain of dependent loads overlaps the wait
+      const double* Zt[2] = {nullptr, nullptr};
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        if (oidx[h] < 0 || emode == 1) continue;
+        const int zp = find(a.zbits, a.zrowptr, Ia, J0 + bt0 + h);
+        if (zp < 0) continue;
+        const int64_t zi = (int64_t)(a.zref[zp] & ~REF_T);
+        Zt[h] = a.zpool + (int64_t)(a.zslot ? a.zslot[zi] : zi) * TE;
+        prefetch_l2(Zt[h] + r * TB);
+        prefetch_l2(Zt[h] + r * TB + 16);
+      }
       // phase 1, once per accumulation segment: TMEM -> the exact fixed-point
       // sums of this thread's row in the scratch (the first segment stores, the
       // others add), then the segment's TMEM blocks go back to the MMA issuer
@@ -1068,12 +1143,12 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             }
 #pragma unroll
             for (int gg = 0; gg < 4; ++gg) {   // relative groups of the window
-              if (gg <= a.ghi - a.glo && ((written >> gg) & 1u)) {   // warp-uniform: groups no product reached are zero
+              if (gg <= ghi - glo && ((written >> gg) & 1u)) {   // warp-uniform: groups no product reached are zero
                 float g[16];
                 const uint32_t blk = (gm >> (8 + 2 * gg)) & 3u;
                 tmem_ld16(tmem + ((uint32_t)(quarter * 32) << 16) + blk * ST + (uint32_t)col0, g);
 #pragma unroll
-                for (int i = 0; i < 16; ++i) fx[i] += f32_int_to_ll(g[i]) * (1ll << (W * (a.ghi - a.glo - gg)));
+                for (int i = 0; i < 16; ++i) fx[i] += f32_int_to_ll(g[i]) * (1ll << (W * (ghi - glo - gg)));
               }
             }
 #pragma unroll
@@ -1095,13 +1170,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
         const int Jb = J0 + bt;
         const int oi = oidx[h];
         if (oi < 0) continue;
-        // Z_IJ (X~_IJ in the forward step; absent -> 0)
-        const double* Zt = nullptr;
-        const int zp = a.emode == 1 ? -1 : find(a.zbits, a.zrowptr, Ia, Jb);
-        if (zp >= 0) {
-          const int64_t zi = (int64_t)(a.zref[zp] & ~REF_T);
-          Zt = a.zpool + (int64_t)(a.zslot ? a.zslot[zi] : zi) * TE;
-        }
+        const double* Z = Zt[h];
         double trS = 0.0, trX = 0.0, n2 = 0.0, e2 = 0.0;
         double* O = a.opool + (int64_t)oi * TE;
         for (int ch = 0; ch < 2; ++ch) {     // 16 columns per chunk
@@ -1109,8 +1178,8 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           double zv[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) zv[i] = 0.0;
-          if (Zt) {
-            const double2* zp = reinterpret_cast<const double2*>(Zt + r * TB + ch * 16);
+          if (Z) {
+            const double2* zp = reinterpret_cast<const double2*>(Z + r * TB + ch * 16);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
               const double2 t2 = zp[i];
@@ -1130,7 +1199,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
           double prev[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) prev[i] = 0.0;
-          if (a.emode == 2) {
+          if (emode == 2) {
             const double2* pp = reinterpret_cast<const double2*>(O + r * TB + ch * 16);
 #pragma unroll
             for (int i = 0; i < 8; ++i) {
@@ -1149,11 +1218,11 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             const double z = inside ? zv[i] : 0.0;
             const bool dg = inside && gi == gj;
             const double S0 = int_times_pow2(fxd, lsu);      // fx * su
-            if (a.emode == 1) { out[i] = S0; continue; }     // finer groups only: S is stored
+            if (emode == 1) { out[i] = S0; continue; }     // finer groups only: S is stored
             // the diagonal of S = X~^2 is the squared row norm, taken in FP64
             // (its digit products are all positive and pass the exact range
             // of the FP32 group sums on dense rows)
-            const double S = (dg && a.dsq) ? a.dsq[gi] : (a.emode == 2 ? S0 + prev[i] : S0);
+            const double S = (dg && a.dsq) ? a.dsq[gi] : (emode == 2 ? S0 + prev[i] : S0);
             double xn;
             // c2 S = (c2 su) fx exactly (su is a power of two)
             if (form == 1) xn = S;
@@ -1169,7 +1238,7 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
 #pragma unroll
           for (int i = 0; i < 8; ++i) op[i] = make_double2(out[2 * i], out[2 * i + 1]);
         }
-        if (a.emode == 1) continue;
+        if (emode == 1) continue;
         // warp reductions (the tile's 32 rows are this warp's 32 lanes)
         for (int o = 16; o > 0; o >>= 1) {
           e2 += __shfl_xor_sync(FULLW, e2, o);
@@ -1205,8 +1274,8 @@ inline unsigned grid_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t);
 size_t panel_record_bytes(int k) { return (size_t)k * UNIT_BYTES; }
 
 cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32_t* slot, const double* pool,
-                                void* data, uint8_t* head, int k, int32_t* err, double scale, bool report_range,
-                                cudaStream_t st) {
+                                void* data, uint8_t* head, int k, int32_t* err, double* rsq, double scale,
+                                bool report_range, cudaStream_t st) {
   if (nrec == 0) return cudaSuccess;
   const uint4* ix = reinterpret_cast<const uint4*>(index);
   __half* d = static_cast<__half*>(data);
@@ -1214,10 +1283,10 @@ cudaError_t launch_panel_slices(const uint32_t* index, int64_t nrec, const int32
   const int rr = report_range ? 1 : 0;
   const unsigned g = (unsigned)nrec;
   ++g_launches;
-  if (k == 2) k_panel_slices<2><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
-  else if (k == 3) k_panel_slices<3><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
-  else if (k == 5) k_panel_slices<5><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
-  else k_panel_slices<4><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, ls, rr);
+  if (k == 2) k_panel_slices<2><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, rsq, ls, rr);
+  else if (k == 3) k_panel_slices<3><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, rsq, ls, rr);
+  else if (k == 5) k_panel_slices<5><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, rsq, ls, rr);
+  else k_panel_slices<4><<<g, 256, 0, st>>>(ix, slot, pool, d, head, err, rsq, ls, rr);
   return cudaGetLastError();
 }
 
@@ -1246,11 +1315,11 @@ __global__ void k_panel_fill(const int32_t* __restrict__ frowptr, const int32_t*
   }
 }
 
-cudaError_t launch_row_sq(const FullPattern& fp, const int32_t* slot, const double* pool, int nb, int64_t n,
-                          double* dsq, cudaStream_t st) {
-  if (nb == 0) return cudaSuccess;
+cudaError_t launch_row_sq_sum(const int32_t* spos, int nsr, int words, const double* rsq, int64_t n, double* dsq,
+                              cudaStream_t st) {
+  if (nsr == 0) return cudaSuccess;
   ++g_launches;
-  k_row_sq<<<grid_for((int64_t)nb * 32, 256), 256, 0, st>>>(fp.rowptr, fp.ref, slot, pool, nb, n, dsq);
+  k_row_sq_sum<<<(unsigned)nsr, 128, 0, st>>>(spos, words, rsq, n, dsq);
   return cudaGetLastError();
 }
 

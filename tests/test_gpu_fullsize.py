@@ -72,3 +72,60 @@ def test_water24k_mixed_matches_fp64(water24k):
     err = np.sqrt(tot)
     print(f"water N=24000: ||D_split16 - D_fp64||_F = {err:.3e}")
     assert err <= 1e-6
+
+
+# ----------------------------------------------------------------- the headline size: N = 192000, tau = 1e-5
+def _symv(brow, bcol, val, v):
+    """y = A v for the symmetric matrix whose upper tiles are given (torch, on
+    the device): every stored tile (I, J) adds A_IJ v_J to y_I and, off the
+    diagonal, A_IJ^T v_I to y_J.  v: [nb * 32, m]."""
+    import torch
+    nb = v.shape[0] // 32
+    V = v.view(nb, 32, -1)
+    Y = torch.zeros_like(V)
+    I, J = brow.long(), bcol.long()
+    for lo in range(0, brow.numel(), 1 << 18):     # chunks keep the temporaries small
+        sl = slice(lo, lo + (1 << 18))
+        t = val[sl]
+        Y.index_add_(0, I[sl], torch.bmm(t, V[J[sl]]))
+        off = I[sl] != J[sl]
+        Y.index_add_(0, J[sl][off], torch.bmm(t[off].transpose(1, 2), V[I[sl][off]]))
+    return Y.view(nb * 32, -1)
+
+
+def test_water192k_properties_on_the_tensor_path():
+    # the bench's workload and path (four FP16 slices): idempotency and D F = F D
+    # checked with block-sparse products on random vectors, trace against nocc,
+    # symmetric diagonal tiles; the FP64 comparison at this size is in bench.py
+    import torch
+    import paper_1909_12533_gb300 as sp2
+    c = make_config(3)
+    F = c["F"]
+    n, nb = F.n, F.nb
+    ctx = sp2.SP2(F, c["nocc"], c["homo_ub"], c["lumo_lb"], c["tau"], stop=c["stop"], precision="split16")
+    st = ctx.run()
+    brow, bcol, val = ctx.D_device()
+    ctx.close()
+    assert ctx.code == 0 and st["converged"]
+    assert bool((brow <= bcol).all())
+    diag = brow == bcol
+    assert float((val[diag] - val[diag].transpose(1, 2)).abs().max()) <= 1e-12
+    tr = float(val[diag].diagonal(dim1=1, dim2=2).sum())
+    e_n = st["e"][-1]
+    assert abs(tr - c["nocc"]) <= np.sqrt(n) * e_n + 1e-6
+    g = torch.Generator("cuda").manual_seed(3)
+    v = torch.randn(nb * 32, 4, dtype=torch.float64, device="cuda", generator=g)
+    v[n:] = 0.0
+    Fb = torch.from_numpy(F.brow).cuda()
+    Fc = torch.from_numpy(F.bcol).cuda()
+    Fv = torch.from_numpy(F.val).cuda()
+    Dv = _symv(brow, bcol, val, v)
+    DDv = _symv(brow, bcol, val, Dv)
+    idem = float((DDv - Dv).norm() / v.norm())
+    comm = float((_symv(brow, bcol, val, _symv(Fb, Fc, Fv, v)) - _symv(Fb, Fc, Fv, Dv)).norm()
+                 / _symv(Fb, Fc, Fv, v).norm())
+    print(f"water N=192000 split16: n = {st['n']}, e_n = {e_n:.2e}, trace - nocc = {tr - c['nocc']:.2e}, "
+          f"||D^2 v - D v|| / ||v|| = {idem:.2e}, ||DFv - FDv|| / ||Fv|| = {comm:.2e}")
+    # a random unit vector sees ||D^2 - D||_F / sqrt(N) of the idempotency error
+    assert idem <= 10 * e_n / np.sqrt(n) * np.sqrt(4) + 1e-9
+    assert comm < 1e-5

@@ -180,6 +180,58 @@ def X_n2(tiles, t):
     return next(v for i, j, v in tiles if (i, j) == t)
 
 
+def _dyadic_tiles(norm2, big):
+    """Symmetric 128 x 128 matrix whose upper tile (I, J) has squared Frobenius
+    norm norm2[(I, J)] * 2^-60 exactly (integer units; tiles not listed get
+    `big`): each tile is a sum of squares of integers a * 2^-30 placed on the
+    tile's own diagonal (mirrored for I < J), so every sum below is exact."""
+    X = np.zeros((128, 128))
+    for I in range(4):
+        for J in range(I, 4):
+            rem = norm2.get((I, J), big)
+            r = 0
+            while rem > 0:                      # greedy squares, at most 32 terms
+                a = math.isqrt(rem)
+                X[32 * I + r, 32 * J + r] = X[32 * J + r, 32 * I + r] = a * 2.0 ** -30
+                rem -= a * a
+                r += 1
+            assert r <= 32
+    return X
+
+
+@pytest.mark.parametrize("slack", ["2^-30", "0"])
+def test_truncation_cut_at_the_budget_real_number_rule(slack):
+    # Section 2 / Eq. (8), read as: drop the longest prefix (ascending norms)
+    # with sum w ||X_IJ||_F^2 <= tau^2.  The oracle sums shares rounded up to
+    # units of tau^2 2^-36.  Five candidate tiles (weights 2, 2, 1, 2, 1) sum to
+    # tau^2 (1 - 2^-30) or to tau^2 exactly; every share has a fractional part
+    tau = 2.0 ** -10                       # tau^2 = 2^-20 = 2^40 units of 2^-60
+    cand = [((0, 1), 2, 2 ** 34 + 3), ((0, 2), 2, 2 ** 35 + 5), ((1, 1), 1, 2 ** 35 + 2 ** 34 + 7),
+            ((2, 3), 2, 2 ** 36 + 9)]
+    target = 2 ** 40 - (2 ** 10 if slack == "2^-30" else 0)
+    last = target - sum(w * v for _, w, v in cand)
+    assert cand[-1][2] < last < 2 ** 44
+    cand.append(((3, 3), 1, last))
+    X = _dyadic_tiles({t: v for t, _, v in cand}, big=2 ** 44)
+    # the plain rule, in exact integers: all five fit (sum <= tau^2), a sixth does not
+    assert sum(w * v for _, w, v in cand) <= 2 ** 40
+    assert sum(w * v for _, w, v in cand) + 2 ** 44 > 2 ** 40
+    assert all((w * v) % 16 for _, w, v in cand)          # shares (units tau^2 2^-36) are not integers
+    _, kept, dropped = O.truncate_select(X, tau, "frobenius")
+    E2 = float(np.sum(_E(X, dropped) ** 2))               # exact: multiples of 2^-60 below 2^-20
+    assert E2 <= tau * tau
+    if slack == "2^-30":
+        # 64 units of slack against at most 5 units of rounding: the readings agree
+        assert sorted(dropped) == sorted(t for t, _, _ in cand)
+        assert E2 == (2 ** 40 - 2 ** 10) * 2.0 ** -60
+    else:
+        # ||E||_F = tau exactly for the plain rule; the rounded-up shares exceed
+        # the budget by at most 5 units, so the oracle keeps the fifth tile (it
+        # is conservative by less than one unit per candidate tile)
+        assert sorted(dropped) == sorted(t for t, _, _ in cand[:4])
+        assert E2 < tau * tau
+
+
 def test_truncation_tau_zero_drops_only_zero_tiles():
     rng = np.random.default_rng(6)
     X = _sym(rng, 96)
