@@ -297,19 +297,20 @@ __global__ void __launch_bounds__(256, 5) k_panel_slices(const uint4* __restrict
     const bool tr = (wd[q] & REF_T) != 0;
     rs[q] = 0.0;
     if (rsq) {
-      double v[PER];
+      // FP64 is scarce on this part: squares and sums as fused multiply-adds
+      double x[PER];
 #pragma unroll
-      for (int k = 0; k < PER; ++k) {
-        const double x = __longlong_as_double(xb[q][k]);
-        v[k] = x * x;
-      }
+      for (int k = 0; k < PER; ++k) x[k] = __longlong_as_double(xb[q][k]);
       if (tr) {
-        rs[q] = (v[0] + v[1]) + (v[2] + v[3]);
+        rs[q] = fma(x[3], x[3], fma(x[2], x[2], fma(x[1], x[1], x[0] * x[0])));
       } else {
-        // reduce-scatter of the 4 rows over the lanes
+        // reduce-scatter of the 4 rows over the lanes (the first step
+        // exchanges the elements, the others the partial sums)
         const bool b16 = (lane & 16) != 0, b8 = (lane & 8) != 0;
-        const double h0 = (b16 ? v[2] : v[0]) + __shfl_xor_sync(0xffffffffu, b16 ? v[0] : v[2], 16);
-        const double h1 = (b16 ? v[3] : v[1]) + __shfl_xor_sync(0xffffffffu, b16 ? v[1] : v[3], 16);
+        const double o0 = __shfl_xor_sync(0xffffffffu, b16 ? x[0] : x[2], 16);
+        const double o1 = __shfl_xor_sync(0xffffffffu, b16 ? x[1] : x[3], 16);
+        const double m0 = b16 ? x[2] : x[0], m1 = b16 ? x[3] : x[1];
+        const double h0 = fma(m0, m0, o0 * o0), h1 = fma(m1, m1, o1 * o1);
         double t = (b8 ? h1 : h0) + __shfl_xor_sync(0xffffffffu, b8 ? h0 : h1, 8);
         t += __shfl_xor_sync(0xffffffffu, t, 4);
         t += __shfl_xor_sync(0xffffffffu, t, 2);
@@ -1209,36 +1210,58 @@ __global__ void __launch_bounds__(TC_THREADS, 1) k_square_tc(TcArgs a) {
             }
           }
           double out[16];
+          if (Z || form == 0) {
 #pragma unroll
-          for (int i = 0; i < 16; ++i) {
-            const int c = ch * 16 + i;
-            const int64_t gj = (int64_t)Jb * TB + c;
-            const bool inside = gi < a.n && gj < a.n;
-            const double fxd = inside ? (double)fx[i] : 0.0;
-            const double z = inside ? zv[i] : 0.0;
-            const bool dg = inside && gi == gj;
-            const double S0 = int_times_pow2(fxd, lsu);      // fx * su
-            if (emode == 1) { out[i] = S0; continue; }     // finer groups only: S is stored
-            // the diagonal of S = X~^2 is the squared row norm, taken in FP64
-            // (its digit products are all positive and pass the exact range
-            // of the FP32 group sums on dense rows)
-            const double S = (dg && a.dsq) ? a.dsq[gi] : (emode == 2 ? S0 + prev[i] : S0);
-            double xn;
-            // c2 S = (c2 su) fx exactly (su is a power of two)
-            if (form == 1) xn = S;
-            else if (form == 2) xn = twice(z) - S;
-            else xn = fma(a.c2, S, fma(a.c1, z, dg ? a.c0 : 0.0));
-            out[i] = xn;
-            const double df = z - S;
-            e2 = fma(df, df, e2);
-            n2 = fma(xn, xn, n2);
-            if (dg) { trS += S; trX += z; }
+            for (int i = 0; i < 16; ++i) {
+              const int c = ch * 16 + i;
+              const int64_t gj = (int64_t)Jb * TB + c;
+              const bool inside = gi < a.n && gj < a.n;
+              const double fxd = inside ? (double)fx[i] : 0.0;
+              const double z = inside ? zv[i] : 0.0;
+              const bool dg = inside && gi == gj;
+              const double S0 = int_times_pow2(fxd, lsu);      // fx * su
+              if (emode == 1) { out[i] = S0; continue; }     // finer groups only: S is stored
+              // the diagonal of S = X~^2 is the squared row norm, taken in FP64
+              // (its digit products are all positive and pass the exact range
+              // of the FP32 group sums on dense rows)
+              const double S = (dg && a.dsq) ? a.dsq[gi] : (emode == 2 ? S0 + prev[i] : S0);
+              double xn;
+              // c2 S = (c2 su) fx exactly (su is a power of two)
+              if (form == 1) xn = S;
+              else if (form == 2) xn = twice(z) - S;
+              else xn = fma(a.c2, S, fma(a.c1, z, dg ? a.c0 : 0.0));
+              out[i] = xn;
+              const double df = z - S;
+              e2 = fma(df, df, e2);
+              n2 = fma(xn, xn, n2);
+              if (dg) { trS += S; trX += z; }
+            }
+          } else {
+            // no X~ tile here (z = 0) and X_new = S or 2 z - S = -S: every
+            // (z - S)^2 equals xn^2, so one FMA per element gives both sums
+            // (e2 is set from n2 below; the same values in the same order)
+#pragma unroll
+            for (int i = 0; i < 16; ++i) {
+              const int c = ch * 16 + i;
+              const int64_t gj = (int64_t)Jb * TB + c;
+              const bool inside = gi < a.n && gj < a.n;
+              const double fxd = inside ? (double)fx[i] : 0.0;
+              const bool dg = inside && gi == gj;
+              const double S0 = int_times_pow2(fxd, lsu);
+              if (emode == 1) { out[i] = S0; continue; }
+              const double S = (dg && a.dsq) ? a.dsq[gi] : (emode == 2 ? S0 + prev[i] : S0);
+              const double xn = form == 1 ? S : 0.0 - S;
+              out[i] = xn;
+              n2 = fma(xn, xn, n2);
+              if (dg) trS += S;
+            }
           }
           double2* op = reinterpret_cast<double2*>(O + r * TB + ch * 16);
 #pragma unroll
           for (int i = 0; i < 8; ++i) op[i] = make_double2(out[2 * i], out[2 * i + 1]);
         }
         if (emode == 1) continue;
+        if (!Z && form != 0) e2 = n2;
         // warp reductions (the tile's 32 rows are this warp's 32 lanes)
         for (int o = 16; o > 0; o >>= 1) {
           e2 += __shfl_xor_sync(FULLW, e2, o);
