@@ -552,7 +552,7 @@ constexpr uint32_t REC_LAST = 1u << 17;   // no more super-tiles (no data)
 constexpr uint32_t REC_SEG = 1u << 18;    // end of an accumulation segment of the super-tile (no data)
 constexpr uint32_t SEG_LAST = 1u << 31;   // segment record flag: last segment of its super-tile
 constexpr int SEG_RING = 4;               // accumulation segments in flight between MMA and epilogue
-constexpr int NSLOT = 2;                  // tiles in flight between the producer and the epilogue (3 measured 13% slower)
+constexpr int NSLOT = 3;                  // tiles in flight between the producer and the epilogue (2: 3% slower, 4: same)
 constexpr int SEG_KSTEPS = 16;            // K steps per accumulation segment of a segmented tile (default)
 
 // record header byte: first nonzero slice (bits 0-2), tiles present (bits 4-7)
