@@ -59,7 +59,7 @@ PEAK_FP64_TFLOPS = 1.25   # GB300 FP64 nominal (no FP64 tensor path on this chip
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum, mean bytes per launch) of the
 # square kernel from one ncu capture of the default workload, keyed by the sha256 prefix of the
 # kernel source it was taken on; reported only while the source is unchanged.
-SQUARE_TC_TRAFFIC = {("water24k", 4): ("00086e7fad37915b", 13.979e9)}
+SQUARE_TC_TRAFFIC = {("water192k", 4): ("c06adb9cb13d2605", 270.23e9)}
 
 
 def _source_hash(name: str) -> str:
