@@ -299,37 +299,18 @@ def main(argv=None) -> int:
         ms_max, flops_all = ms, flops
     value = flops_all / (ms_max / 1e3) / 1e12
 
-    # accuracy of this path, and the FP64 GPU path timed on the same workload
-    st_main, D_main = step(Dev, args.precision, keep_D=True)
-    fp64 = None
-    err = None
-    if args.precision != "fp64" and not args.no_fp64_compare:
-        torch.cuda.synchronize()
-        f0 = torch.cuda.Event(enable_timing=True)
-        f1 = torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        st64, D64 = step(Dev, "fp64", keep_D=True)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1)
-        err = _tile_diff_norm(D_main, D64, nb)
-        fp64 = {"time_to_D_ms": ms64, "eff_tflops": st64["alg_flops"] / ms64 / 1e9, "iterations": st64["n"],
-                "steps": 1, "warmup": 0, "nnzb_final": st64["nnzb_final"],
-                "speedup_of_mixed": ms64 / (ms_max / args.steps)}
-    accuracy = {"D_minus_D_fp64_F": err, "trace_minus_nocc": _trace(D_main, Fh.n) - c["nocc"],
-                "idempotency_e_n": st_main["e"][st_main["n"]], "iterations": st_main["n"],
-                "ref": "FP64 GPU path (itself bit-for-bit parity-tested against the CPU oracle)"}
-
     e2e = None
     if not args.no_e2e:
         # through the public API from pinned host memory: every step uploads F, runs, and
-        # copies D back into pinned host buffers (buffers filled / allocated before timing)
+        # copies D back into pinned host buffers (buffers filled / allocated before timing);
+        # measured right after the device-timed steps, before the accuracy and FP64 runs,
+        # which keep their D on the device
         class HostF:
             n = Fh.n
             brow = torch.from_numpy(Fh.brow).pin_memory()
             bcol = torch.from_numpy(Fh.bcol).pin_memory()
             val = torch.from_numpy(Fh.val).pin_memory()
-        cap = int(st_main["nnzb_final"] * 1.25) + 1024
+        cap = int(stats[-1]["nnzb_final"] * 1.25) + 1024
         Dh = (torch.empty(cap, dtype=torch.int32).pin_memory(), torch.empty(cap, dtype=torch.int32).pin_memory(),
               torch.empty((cap, 32, 32), dtype=torch.float64).pin_memory())
 
@@ -353,6 +334,27 @@ def main(argv=None) -> int:
         e2e = {"value": sum(r[0]["alg_flops"] for r in runs) / args.steps / dt / 1e12, "unit": "TFLOP/s",
                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h), "seconds_per_step": dt,
                "host_buffers": "pinned"}
+
+    # accuracy of this path, and the FP64 GPU path timed on the same workload
+    st_main, D_main = step(Dev, args.precision, keep_D=True)
+    fp64 = None
+    err = None
+    if args.precision != "fp64" and not args.no_fp64_compare:
+        torch.cuda.synchronize()
+        f0 = torch.cuda.Event(enable_timing=True)
+        f1 = torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        st64, D64 = step(Dev, "fp64", keep_D=True)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        err = _tile_diff_norm(D_main, D64, nb)
+        fp64 = {"time_to_D_ms": ms64, "eff_tflops": st64["alg_flops"] / ms64 / 1e9, "iterations": st64["n"],
+                "steps": 1, "warmup": 0, "nnzb_final": st64["nnzb_final"],
+                "speedup_of_mixed": ms64 / (ms_max / args.steps)}
+    accuracy = {"D_minus_D_fp64_F": err, "trace_minus_nocc": _trace(D_main, Fh.n) - c["nocc"],
+                "idempotency_e_n": st_main["e"][st_main["n"]], "iterations": st_main["n"],
+                "ref": "FP64 GPU path (itself bit-for-bit parity-tested against the CPU oracle)"}
 
     if rank != 0:
         return 0
