@@ -14,7 +14,11 @@
 // rounding error is scaled down by 2^-11 per group.  The epilogue combines the
 // groups as an exact int64 fixed-point sum and converts once to FP64.  Pairs
 // with s + t <= k + 1 are used (k = 4: 10 MMAs per K step, error ~2^-44 per
-// element; k = 2 is the three-product hi+lo form).
+// element; k = 2 is the three-product hi+lo form).  Two places where the FP32
+// sums would not stay exact are handled apart: the diagonal of S = X~^2, whose
+// products of equal slices are all positive, is taken from FP64 squared row
+// norms summed while the records are sliced; and long K loops (dense rows) are
+// accumulated in segments whose exact sums the epilogue adds in int64.
 //
 // Operands are stored panel by panel: for a super-row R (tile rows 4R..4R+3)
 // and a K tile present in any of its rows, one record holds slice s of the 4
