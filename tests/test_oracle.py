@@ -466,6 +466,33 @@ def test_stopping_criterion_fires_at_noise_floor():
     assert abs(r.n - ri.n) <= 2
 
 
+@pytest.mark.parametrize("accelerate", [False, True])
+def test_homo_lumo_estimates_invert_a_single_eigenvalue(accelerate):
+    # Section 4 Step 3: the estimate turns r = x - x^2 of an eigenvalue's image
+    # x = x_j back into x (the root on the eigenvalue's side of 1/2) and pulls
+    # it back through f_j .. f_1 and X_0's map.  The e_j, t_j that one
+    # eigenvalue alone produces (its images by poly_scalar, pinned against the
+    # matrix polynomials above; steps whose r is below 1e-6, where x - x^2
+    # loses its digits in FP64, are left out as below the noise threshold)
+    # must give that eigenvalue back
+    import dataclasses
+    c = make_config(1)
+    nocc, ev = c["nocc"], c["eigenvalues"]
+    res = O.sp2(c["F"], nocc, c["homo_ub"], c["lumo_lb"], tau=0.0, stop="idempotency", accelerate=accelerate)
+    sch = res.sched
+    width = sch.lmax - sch.lmin
+    for lam, side in ((ev[nocc - 1], 0), (ev[nocc], 1)):
+        x = (sch.lmax - lam) / width
+        r = [x - x * x]
+        for j in range(1, res.n + 1):
+            x = O.poly_scalar(sch.p[j], sch.alpha[j], x)
+            r.append(x - x * x)
+        r = [v if v >= 1e-6 else 0.0 for v in r]
+        est = O.homo_lumo_estimates(dataclasses.replace(res, e=list(r), t=list(r)), c["F"].shape[0])
+        assert est[side] is not None
+        assert abs(est[side] - lam) <= 1e-11 * width, (side, est[side], lam)
+
+
 def test_homo_lumo_estimates_approximate():
     # approximately pinned: plain SP2 estimates near the exact homo/lumo
     c = make_config(1)
