@@ -72,6 +72,21 @@ def _source_hash(name: str) -> str:
     return hashlib.sha256(code.encode()).hexdigest()[:16]
 
 
+def aggregate_ranks(ms: float, flops: float, world: int, device: str = "cuda") -> tuple[float, float]:
+    """Whole-job figures of a replicated run (each rank an independent replica):
+    the slowest rank's time and the sum of all ranks' flops (collectives of the
+    initialised process group; a single rank returns its own figures)."""
+    if world <= 1:
+        return ms, flops
+    import torch
+    import torch.distributed as dist
+    mx = torch.tensor([ms], dtype=torch.float64, device=device)
+    sm = torch.tensor([flops], dtype=torch.float64, device=device)
+    dist.all_reduce(mx, op=dist.ReduceOp.MAX)
+    dist.all_reduce(sm, op=dist.ReduceOp.SUM)
+    return float(mx[0]), float(sm[0])
+
+
 def measured_peaks() -> dict:
     p = ROOT / "MEASURED_PEAKS.json"
     if p.exists():
@@ -293,15 +308,7 @@ def main(argv=None) -> int:
     squares = sum(s["squares"] for s in stats)
     hw = sum(s["tc_hw_flops"] for s in stats)
     launches = sum(s["kernel_launches"] for s in stats)
-    t = torch.tensor([ms, flops], dtype=torch.float64, device="cuda")
-    if world > 1:
-        mx = t.clone()
-        torch.distributed.all_reduce(mx[:1], op=torch.distributed.ReduceOp.MAX)
-        sm = t.clone()
-        torch.distributed.all_reduce(sm[1:], op=torch.distributed.ReduceOp.SUM)
-        ms_max, flops_all = float(mx[0]), float(sm[1])
-    else:
-        ms_max, flops_all = ms, flops
+    ms_max, flops_all = aggregate_ranks(ms, flops, world)
     value = flops_all / (ms_max / 1e3) / 1e12
 
     e2e = None
